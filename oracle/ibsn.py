@@ -9,8 +9,11 @@ Readings where the paper is silent or garbled (same list as the design notes):
   R1  ||.|| is the Euclidean norm everywhere (Sec. 1 notation).
   R2  Newton system sign: Alg. 2 (Delta = -(H_rho + ||g|| I)^{-1} g).
   R3  The Newton system is solved by Jacobi-preconditioned CG from 0, stopped
-      when ||r|| <= min(cg_rtol, ||g||) * ||g|| or after max_cg iterations;
-      the direction is then centred (L^k is invariant to gamma + c 1).
+      when ||r|| <= rtol ||g||, rtol = min(cg_rtol, max(||g||, mu_k / (4 ||g||))),
+      or after max_cg iterations: the superlinear forcing term ||g||, relaxed
+      to the accuracy at which the linear model already predicts the next
+      gradient below the gate mu_k of Eq. 8; the direction is then centred
+      (L^k is invariant to gamma + c 1).
   R4  Armijo starts at t = 1, shrinks by beta, at most max_armijo trials.
   R5  Newton phase stop (Eq. 8): gate ||g|| < mu_k, then
       D_phi(Proj(X), X) <= min(m, n) * mu_k, mu_k = max(1e-4/(k+1)^2, 1e-11).
@@ -151,14 +154,21 @@ def pcg(A: np.ndarray, rhs: np.ndarray, diag: np.ndarray, rtol: float, maxit: in
     return x, it, float(rnorm)
 
 
-def newton_direction(H_rho, g, cg_rtol: float, max_cg: int):
+def cg_tolerance(gnorm: float, cg_rtol: float, mu: float | None) -> float:
+    """Relative CG tolerance of reading R3."""
+    if mu is None or gnorm == 0.0:
+        return min(cg_rtol, gnorm)
+    return min(cg_rtol, max(gnorm, 0.25 * mu / gnorm))
+
+
+def newton_direction(H_rho, g, cg_rtol: float, max_cg: int, mu: float | None = None):
     """Delta = -(H_rho + ||g|| I)^{-1} g (Alg. 2), by Jacobi PCG, then centred (R3).
 
     Returns (Delta, cg_iterations).
     """
     gnorm = float(np.linalg.norm(g))
     A = H_rho + gnorm * np.eye(len(g))
-    rtol = min(cg_rtol, gnorm)
+    rtol = cg_tolerance(gnorm, cg_rtol, mu)
     delta, it, _ = pcg(A, -g, np.diag(A).copy(), rtol, max_cg)
     delta = delta - delta.mean()
     return delta, it
@@ -355,7 +365,7 @@ def ibsn(C, a, b, params: IBSNParams, gamma0=None, record=False) -> IBSNResult:
                 H = sparsified_hessian(sparsify_plan(P, a, rho), a, eta)
             else:
                 H = hessian(P, a, eta)
-            delta, cg_it = newton_direction(H, g, params.cg_rtol, params.max_cg)
+            delta, cg_it = newton_direction(H, g, params.cg_rtol, params.max_cg, mu)
             tot_cg += cg_it
             t, _, _ = armijo(logX, C, a, b, eta, gamma, delta, g, params.sigma, params.beta, params.max_armijo)
             if record:

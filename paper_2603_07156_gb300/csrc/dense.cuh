@@ -1,0 +1,913 @@
+// Dense m x n row passes of IBSN.  Each block owns a contiguous range of rows
+// and streams them once; one row at a time is held in registers, spread over
+// the block's TG threads (thread t owns columns (s*TG + t)*V + e, s < CH,
+// e < V).  Row reductions are block reductions; column sums are accumulated
+// per thread in registers (float: Kahan) or in shared memory (double) and
+// written once per block as a partial, reduced deterministically afterwards.
+//
+// The exponent of every pass is x_ij = K_ij + d_j, where K is the anchored
+// matrix built by k_reanchor and d_j = (gamma_j - gamma^anc_j)/eta, so that
+// P^k(gamma)_ij = exp(x_ij - lse_i) (Eq. 6).
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ibsn {
+
+template <typename T>
+struct DenseArgs {
+  const T* K;
+  int64_t ldk;
+  int m, n, rows_per_block, istar;
+  const T* dv;         // d_j, padded with 0 to ldk
+  const T* v1;         // per-column input 1 (variant specific)
+  const T* v2;         // per-column input 2
+  const T* v3;         // per-column input 3
+  const double* a;     // m
+  double* rowout;      // m, variant specific (lse, e_r, zeta)
+  double* rowout2;     // m
+  double* colpart;     // gridDim.x x ldk
+  double* rowpart;     // gridDim.x x kRowParts
+  double s1, s2;       // scalars (variant specific)
+  // sparsify
+  int32_t* pool_col;
+  T* pool_val;
+  int64_t* row_start;
+  int32_t* row_len;
+  int32_t* blkcnt;     // gridDim.x x ldk
+  T* prow;             // row i* of P (dense, n)
+  unsigned long long* pool_top;
+  int64_t cap;
+  int* err;
+  // cost access (certify / reanchor)
+  CostRef cost;
+  const double* gam;   // gamma (certify)
+  const double* wv;    // reanchor: log b_j + (Gamma_j + gamma_j)/eta
+  double lam;          // reanchor: (k+1)/eta
+  T* Kout;             // reanchor output
+  double* plan_out;    // certify / export: m x n float64, nullable
+  // float-float passes: K = K (hi plane) + Klo (lo plane); float64 copies of
+  // the per-column inputs for the entries evaluated in float64
+  const float* Klo;
+  float* Klo_out;      // reanchor: lo plane output (nullable)
+  const double* dv64;
+  const double* v1d;
+  const double* v2d;
+  const double* v3d;
+};
+
+template <typename T, int TG, int CH>
+struct Tile {
+  static constexpr int V = VecT<T>::N;
+  T x[CH][V];
+
+  __device__ __forceinline__ static int64_t col(int s) {
+    return (int64_t)(s * TG + (int)threadIdx.x) * V;
+  }
+
+  // x = K_i + d  (padding columns of K hold -inf)
+  __device__ __forceinline__ void load(const T* __restrict__ row, const T* __restrict__ dv, int64_t ldk) {
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = col(s);
+      if (c < ldk) {
+        T kv[V], d[V];
+        load_vec_stream(row + c, kv);
+        load_vec(dv + c, d);
+#pragma unroll
+        for (int e = 0; e < V; ++e) x[s][e] = kv[e] + d[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) x[s][e] = neg_inf<T>();
+      }
+    }
+  }
+
+  __device__ __forceinline__ T local_max() const {
+    T mx = neg_inf<T>();
+#pragma unroll
+    for (int s = 0; s < CH; ++s)
+#pragma unroll
+      for (int e = 0; e < V; ++e) mx = fmax(mx, x[s][e]);
+    return mx;
+  }
+
+  // x <- exp(x - mx), returns the thread's sum
+  __device__ __forceinline__ T exp_shift(T mx) {
+    T ps = T(0);
+#pragma unroll
+    for (int s = 0; s < CH; ++s)
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        x[s][e] = exp_t(x[s][e] - mx);
+        ps += x[s][e];
+      }
+    return ps;
+  }
+};
+
+// Per-thread column accumulators.  float: registers with Kahan compensation;
+// double: shared memory slots owned by the thread (no sharing, no atomics).
+template <typename T, int TG, int CH>
+struct ColAcc {
+  static constexpr int V = VecT<T>::N;
+  static constexpr bool kSmem = std::is_same<T, double>::value;
+  Acc<float> r[kSmem ? 1 : CH][kSmem ? 1 : V];
+  double* sm;
+  int64_t ld;
+
+  __device__ __forceinline__ void init(double* smem, int64_t ldk) {
+    ld = ldk;
+    if constexpr (kSmem) {
+      sm = smem;
+#pragma unroll
+      for (int s = 0; s < CH; ++s) {
+        const int64_t c = Tile<T, TG, CH>::col(s);
+        if (c < ldk)
+#pragma unroll
+          for (int e = 0; e < V; ++e) sm[c + e] = 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < CH; ++s)
+#pragma unroll
+        for (int e = 0; e < V; ++e) r[s][e].zero();
+    }
+  }
+  // columns past the padded row (tile wider than ldk) are not stored
+  __device__ __forceinline__ void add(int s, int e, T v) {
+    if constexpr (kSmem) {
+      const int64_t c = Tile<T, TG, CH>::col(s) + e;
+      if (c < ld) sm[c] += v;
+    } else {
+      r[s][e].add(v);
+    }
+  }
+  __device__ __forceinline__ void flush(double* __restrict__ out, int64_t ldk) {
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      if (c < ldk) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          if constexpr (kSmem) {
+            out[c + e] = sm[c + e];
+          } else {
+            out[c + e] = r[s][e].value();
+          }
+        }
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ void row_range(int m, int rpb, int& r0, int& r1) {
+  r0 = blockIdx.x * rpb;
+  r1 = min(m, r0 + rpb);
+}
+
+// ---------------------------------------------------------------------------
+// Plan pass (Eqs. 6-7): lse_i, c_j = sum_i a_i P_ij, sum_i a_i lse_i.
+// rowout = lse (nullable).
+// ---------------------------------------------------------------------------
+template <typename T, int TG, int CH>
+__global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
+  extern __shared__ double dyn_sm[];
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ T sht[TG / 32];
+  constexpr int V = VecT<T>::N;
+  ColAcc<T, TG, CH> acc;
+  acc.init(dyn_sm, A.ldk);
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  double lpart = 0.0;
+  Tile<T, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const T mx = block_max<TG>(t.local_max(), sht);
+    double S[1] = {(double)t.exp_shift(mx)};
+    block_sum<TG, 1>(S, shd);
+    const double lse = (double)mx + log(S[0]);
+    const double ai = A.a[i];
+    lpart += ai * lse;
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = lse;
+    const T w = (T)(ai / S[0]);
+#pragma unroll
+    for (int s = 0; s < CH; ++s)
+#pragma unroll
+      for (int e = 0; e < V; ++e) acc.add(s, e, w * t.x[s][e]);
+  }
+  acc.flush(A.colpart + (int64_t)blockIdx.x * A.ldk, A.ldk);
+  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = lpart;
+}
+
+// ---------------------------------------------------------------------------
+// Armijo trial (Alg. 2) in difference form.  v1 = em_j = expm1(t Delta_j/eta).
+// Per row s_i = sum_j P_ij em_j; the new plan has row sums exp(lse_i)(1+s_i)
+// and column sums c'_j = sum_i a_i P_ij (1 + em_j)/(1 + s_i).
+// rowpart[0] = sum_i a_i psi(s_i), psi(s) = log1p(s) - s (second order),
+// rowpart[1] = sum_i a_i log1p(s_i).  rowout = new lse (nullable).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double psi_log1p_minus(double s) {
+  // log1p(s) - s; Taylor series for small |s| to avoid cancellation
+  if (fabs(s) < 1e-3) {
+    const double s2 = s * s;
+    return s2 * (-0.5 + s * (1.0 / 3.0 + s * (-0.25 + s * (0.2 - s / 6.0))));
+  }
+  return log1p(s) - s;
+}
+
+template <typename T, int TG, int CH>
+__global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
+  extern __shared__ double dyn_sm[];
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ T sht[TG / 32];
+  constexpr int V = VecT<T>::N;
+  ColAcc<T, TG, CH> acc;
+  acc.init(dyn_sm, A.ldk);
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  double ppsi = 0.0, plog = 0.0;
+  Tile<T, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const T mx = block_max<TG>(t.local_max(), sht);
+    T s1 = T(0), s0 = T(0);
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      T em[V];
+      if (c < A.ldk) {
+        load_vec(A.v1 + c, em);
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) em[e] = T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const T ev = exp_t(t.x[s][e] - mx);
+        t.x[s][e] = ev;
+        s0 += ev;
+        s1 += ev * em[e];
+      }
+    }
+    double S[2] = {(double)s0, (double)s1};
+    block_sum<TG, 2>(S, shd);
+    const double si = S[1] / S[0];
+    const double ai = A.a[i];
+    const double l1p = log1p(si);
+    ppsi += ai * psi_log1p_minus(si);
+    plog += ai * l1p;
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = (double)mx + log(S[0]) + l1p;
+    const T w = (T)(ai / (S[0] * (1.0 + si)));
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      T em[V];
+      if (c < A.ldk) {
+        load_vec(A.v1 + c, em);
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) em[e] = T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < V; ++e) acc.add(s, e, w * (t.x[s][e] + t.x[s][e] * em[e]));
+    }
+  }
+  acc.flush(A.colpart + (int64_t)blockIdx.x * A.ldk, A.ldk);
+  if (threadIdx.x == 0) {
+    A.rowpart[blockIdx.x * kRowParts + 0] = ppsi;
+    A.rowpart[blockIdx.x * kRowParts + 1] = plog;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inexact stopping test (Eq. 8) with the rounding of Alg. 3.
+// v1 = omega_j = 1 - y_j, v2 = e_c,j (raw), s1 = S = ||e_c||_1.
+// e_r,i = a_i sum_j P_ij omega_j (z = 1 because X = diag(a) P has row sums a).
+// D_phi = sum_ij [Xhat log(Xhat/X) - Xhat + X]; each term X h(Xhat/X) >= 0
+// with h(r) = r log r - r + 1.  rowout = e_r (nullable).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T h_of_1pu(T u) {
+  // (1+u) log1p(u) - u; series sum_{k>=2} (-1)^k u^k / (k(k-1)) for small |u|
+  if (fabs(u) < T(1e-2)) {
+    const T u2 = u * u;
+    return u2 * (T(0.5) + u * (T(-1.0 / 6.0) + u * (T(1.0 / 12.0) + u * (T(-1.0 / 20.0) + u * T(1.0 / 30.0)))));
+  }
+  if (u <= T(-1)) return T(1);
+  return (T(1) + u) * log1p(u) - u;
+}
+
+template <typename T, int TG, int CH>
+__global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ T sht[TG / 32];
+  constexpr int V = VecT<T>::N;
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  const double invS = A.s1 > 0.0 ? 1.0 / A.s1 : 0.0;
+  double dpart = 0.0;
+  Tile<T, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const T mx = block_max<TG>(t.local_max(), sht);
+    double S[1] = {(double)t.exp_shift(mx)};
+    block_sum<TG, 1>(S, shd);
+    const T invS0 = (T)(1.0 / S[0]);
+    T po = T(0);
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      if (c < A.ldk) {
+        T om[V];
+        load_vec(A.v1 + c, om);
+#pragma unroll
+        for (int e = 0; e < V; ++e) po += t.x[s][e] * invS0 * om[e];
+      }
+    }
+    double R[1] = {(double)po};
+    block_sum<TG, 1>(R, shd);
+    const double ai = A.a[i];
+    const double er = ai * R[0];
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = er;
+    const T ai_t = (T)ai;
+    const T logai_m = (T)(log(ai) - (double)mx - log(S[0]));  // log X_ij = x_ij + this
+    const T erS = (T)(er * invS);
+    T dl = T(0);
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      if (c < A.ldk) {
+        T om[V], ec[V];
+        load_vec(A.v1 + c, om);
+        load_vec(A.v2 + c, ec);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          if (c + e >= A.n) continue;
+          // Xhat = X y + extra, X = a_i P_ij, extra = e_r,i e_c,j / S
+          const T X = ai_t * (t.x[s][e] * invS0);
+          const T extra = erS * ec[e];
+          const T xh = X * (T(1) - om[e]) + extra;
+          if (xh <= T(0)) {
+            dl += X;                                   // 0 log 0 - 0 + X
+          } else if (extra <= X) {
+            dl += X * h_of_1pu(extra / X - om[e]);     // |u| <= 1: no overflow
+          } else {
+            // extra mass on a cell with tiny X: log X from the exponent
+            T kv[V], d[V];
+            load_vec(A.K + (int64_t)i * A.ldk + c, kv);
+            load_vec(A.dv + c, d);
+            const T logX = kv[e] + d[e] + logai_m;
+            dl += xh * (log(xh) - logX) - xh + X;
+          }
+        }
+      }
+    }
+    double D[1] = {(double)dl};
+    block_sum<TG, 1>(D, shd);
+    dpart += D[0];
+  }
+  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = dpart;
+}
+
+// ---------------------------------------------------------------------------
+// Hessian sparsification (Alg. 1): keep P_ij >= rho (s1), renormalise the kept
+// row to 1, write it to the CSR pool; row i* is written dense to prow.
+// blkcnt[b][j] counts kept entries of block b in column j (for the CSC build).
+// ---------------------------------------------------------------------------
+template <typename T, int TG, int CH>
+__global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ T sht[TG / 32];
+  __shared__ int shi[TG / 32];
+  __shared__ unsigned long long s_base;
+  constexpr int V = VecT<T>::N;
+  int cnt[CH][V];
+#pragma unroll
+  for (int s = 0; s < CH; ++s)
+#pragma unroll
+    for (int e = 0; e < V; ++e) cnt[s][e] = 0;
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  const T rho = (T)A.s1;
+  Tile<T, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const T mx = block_max<TG>(t.local_max(), sht);
+    double S[1] = {(double)t.exp_shift(mx)};
+    block_sum<TG, 1>(S, shd);
+    const T invS0 = (T)(1.0 / S[0]);
+    if (i == A.istar) {
+#pragma unroll
+      for (int s = 0; s < CH; ++s) {
+        const int64_t c = Tile<T, TG, CH>::col(s);
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+          if (c + e < A.n) A.prow[c + e] = t.x[s][e] * invS0;
+      }
+      if (threadIdx.x == 0) {
+        A.row_len[i] = 0;
+        A.row_start[i] = 0;
+      }
+      continue;
+    }
+    int kc = 0;
+    T ks = T(0);
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const T P = t.x[s][e] * invS0;
+        const bool keep = (c + e < A.n) && (P >= rho);
+        t.x[s][e] = keep ? P : T(-1);
+        if (keep) {
+          ++kc;
+          ks += P;
+        }
+      }
+    }
+    double KS[1] = {(double)ks};
+    block_sum<TG, 1>(KS, shd);
+    int total = 0;
+    const int off = block_exclusive_scan<TG>(kc, shi, &total);
+    if (threadIdx.x == 0) {
+      const unsigned long long base = atomicAdd(A.pool_top, (unsigned long long)total);
+      s_base = base;
+      if ((long long)(base + total) > A.cap) atomicExch(A.err, (int)kDevCapacity);
+      A.row_start[i] = (int64_t)base;
+      A.row_len[i] = ((long long)(base + total) > A.cap) ? 0 : total;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+    if ((long long)(base + total) > A.cap) continue;
+    const T inv_ks = (T)(1.0 / KS[0]);
+    int64_t pos = (int64_t)base + off;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        if (t.x[s][e] >= T(0)) {
+          A.pool_col[pos] = (int32_t)(c + e);
+          A.pool_val[pos] = t.x[s][e] * inv_ks;
+          ++pos;
+          cnt[s][e] += 1;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < CH; ++s) {
+    const int64_t c = Tile<T, TG, CH>::col(s);
+    if (c < A.ldk)
+#pragma unroll
+      for (int e = 0; e < V; ++e) A.blkcnt[(int64_t)blockIdx.x * A.ldk + c + e] = cnt[s][e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cost entry C_ij in float64 for the kinds of ibsn_cost_kind.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cost_at(const CostRef& c, int i, int64_t j) {
+  if (c.kind == 0) return __ldg(static_cast<const double*>(c.C) + (int64_t)i * c.ldc + j);
+  if (c.kind == 1) return (double)__ldg(static_cast<const float*>(c.C) + (int64_t)i * c.ldc + j);
+  const int ri = i / c.gw, ci = i - ri * c.gw;
+  const int rj = (int)j / c.gw, cj = (int)j - rj * c.gw;
+  const int dr = ri - rj, dc = ci - cj;
+  return c.scale * (double)(dr * dr + dc * dc);
+}
+
+// ---------------------------------------------------------------------------
+// Certificate (App. A rounding, App. C.1 dual) at X = diag(a) P:
+//   v1 = y_j, v2 = omega_j, v3 = e_c,j / S.
+//   e_r,i = a_i sum_j P_ij omega_j,  Xhat_ij = a_i P_ij y_j + e_r,i e_c,j / S
+//   rowpart: [0] sum_ij C_ij Xhat_ij, [1] sum_i a_i zeta_i,
+//            [2] sum_i |a_i (sum_j P_ij - 1)|, [3] sum_i e_r,i,
+//            [4] <X, C - zeta 1^T - 1 gamma^T>, [5] sum C_ij^2,
+//            [6] sum_i (a_i (sum_j P_ij - 1))^2
+//   colpart: sum_i a_i P_ij y_j;  rowout = zeta (nullable), plan_out nullable.
+// ---------------------------------------------------------------------------
+template <typename T, int TG, int CH>
+__global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
+  extern __shared__ double dyn_sm[];
+  __shared__ double shd[6 * (TG / 32)];
+  __shared__ T sht[TG / 32];
+  constexpr int V = VecT<T>::N;
+  ColAcc<T, TG, CH> acc;
+  acc.init(dyn_sm, A.ldk);
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  double part[7] = {0, 0, 0, 0, 0, 0, 0};
+  Tile<T, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const T mx = block_max<TG>(t.local_max(), sht);
+    double S[1] = {(double)t.exp_shift(mx)};
+    block_sum<TG, 1>(S, shd);
+    const double invS0 = 1.0 / S[0];
+    const double ai = A.a[i];
+    // sweep 1: P row sum, sum P omega, zeta_i = min_j C_ij - gamma_j, sum C^2
+    double psum = 0.0, pom = 0.0, zmin = kInf, c2 = 0.0;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      if (c < A.ldk) {
+        T om[V];
+        load_vec(A.v2 + c, om);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          if (c + e >= A.n) continue;
+          const double P = (double)t.x[s][e] * invS0;
+          psum += P;
+          pom += P * (double)om[e];
+          const double C = cost_at(A.cost, i, c + e);
+          zmin = fmin(zmin, C - A.gam[c + e]);
+          c2 += C * C;
+        }
+      }
+    }
+    double R[3] = {psum, pom, c2};
+    block_sum<TG, 3>(R, shd);
+    const double zeta = -block_max<TG>(-zmin, reinterpret_cast<double*>(shd + 3 * (TG / 32)));
+    const double er = ai * R[1];
+    // sweep 2: primal and complementarity
+    double pr = 0.0, cu = 0.0;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      if (c < A.ldk) {
+        T y[V], ecs[V];
+        load_vec(A.v1 + c, y);
+        load_vec(A.v3 + c, ecs);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          if (c + e >= A.n) continue;
+          const double P = (double)t.x[s][e] * invS0;
+          const double C = cost_at(A.cost, i, c + e);
+          const double F = ai * P * (double)y[e];
+          const double xh = F + er * (double)ecs[e];
+          pr += C * xh;
+          cu += ai * P * (C - zeta - A.gam[c + e]);
+          acc.add(s, e, (T)F);
+          if (A.plan_out != nullptr) A.plan_out[(int64_t)i * A.n + c + e] = xh;
+        }
+      }
+    }
+    double Q[2] = {pr, cu};
+    block_sum<TG, 2>(Q, shd);
+    const double rv = ai * (R[0] - 1.0);
+    part[0] += Q[0];
+    part[1] += ai * zeta;
+    part[2] += fabs(rv);
+    part[3] += er;
+    part[4] += Q[1];
+    part[5] += R[2];
+    part[6] += rv * rv;
+    if (threadIdx.x == 0) {
+      if (A.rowout != nullptr) A.rowout[i] = zeta;
+      if (A.rowout2 != nullptr) A.rowout2[i] = er;
+    }
+  }
+  acc.flush(A.colpart + (int64_t)blockIdx.x * A.ldk, A.ldk);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 7; ++q) A.rowpart[blockIdx.x * kRowParts + q] = part[q];
+}
+
+// ---------------------------------------------------------------------------
+// Anchor build (outer update, Alg. 2): e_ij = w_j - lam C_ij in float64 with
+// w_j = log b_j + (Gamma_j + gamma_j)/eta, lam = (k+1)/eta;
+// K_ij = e_ij - max_l e_il, stored as T; padding columns get -inf.
+// rowout = row maxima (nullable).
+// ---------------------------------------------------------------------------
+template <typename T, int TG, int CH>
+__global__ void __launch_bounds__(TG) k_reanchor(DenseArgs<T> A) {
+  __shared__ double shd[TG / 32];
+  constexpr int V = VecT<T>::N;
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  for (int i = r0; i < r1; ++i) {
+    double ev[CH][V];
+    double mx = -kInf;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        if (c + e < A.n) {
+          ev[s][e] = A.wv[c + e] - A.lam * cost_at(A.cost, i, c + e);
+          mx = fmax(mx, ev[s][e]);
+        } else {
+          ev[s][e] = -kInf;
+        }
+      }
+    }
+    mx = block_max<TG>(mx, shd);
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = mx;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+      if (c < A.ldk) {
+        T kv[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) kv[e] = (c + e < A.n) ? (T)(ev[s][e] - mx) : neg_inf<T>();
+        store_vec(A.Kout + (int64_t)i * A.ldk + c, kv);
+        if constexpr (std::is_same<T, float>::value) {
+          if (A.Klo_out != nullptr) {
+            // float-float split: K = hi + lo with lo = fl32(K - hi)
+            float lo[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+              lo[e] = (c + e < A.n) ? (float)((ev[s][e] - mx) - (double)kv[e]) : 0.f;
+            store_vec(A.Klo_out + (int64_t)i * A.ldk + c, lo);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plan export for checks: P_ij as float64 (m x n), same arithmetic as the passes.
+// ---------------------------------------------------------------------------
+template <typename T, int TG, int CH>
+__global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ T sht[TG / 32];
+  constexpr int V = VecT<T>::N;
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  Tile<T, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const T mx = block_max<TG>(t.local_max(), sht);
+    double S[1] = {(double)t.exp_shift(mx)};
+    block_sum<TG, 1>(S, shd);
+    const T invS0 = (T)(1.0 / S[0]);
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<T, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (c + e < A.n) A.plan_out[(int64_t)i * A.n + c + e] = (double)(t.x[s][e] * invS0);
+    }
+  }
+}
+
+
+// ===========================================================================
+// Float-float passes.  The anchored matrix is held as two float planes,
+// K = Khi + Klo (Klo = fl32(K - Khi)).  A float32 evaluation of every entry
+// decides which entries do not underflow (exp(x - M) > 0 in float32); only
+// those are evaluated in float64 from Khi + Klo + d, and only their Klo is
+// read.  All nonzero contributions are therefore float64; the entries skipped
+// are below exp(-87) of the row maximum.
+// ===========================================================================
+template <int TG, int CH>
+struct FFRow {
+  static constexpr int V = 4;
+  // float64 exponent of entry (s, e) of row i relative to the shift M
+  __device__ __forceinline__ static double x64(const DenseArgs<float>& A, int i, int64_t c, int e, double M) {
+    const int64_t off = (int64_t)i * A.ldk + c + e;
+    return ((double)__ldg(A.K + off) + (double)__ldg(A.Klo + off)) + A.dv64[c + e] - M;
+  }
+};
+
+// plan pass: lse_i, c_j = sum_i a_i P_ij, sum_i a_i lse_i (Eqs. 6-7)
+template <int TG, int CH>
+__global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
+  extern __shared__ double dyn_sm[];
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float sht[TG / 32];
+  constexpr int V = 4;
+  double* sm = dyn_sm;
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
+  __syncthreads();
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  double lpart = 0.0;
+  Tile<float, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const float mx = block_max<TG>(t.local_max(), sht);
+    const double M = (double)mx;
+    t.exp_shift(mx);  // float32 filter values
+    double ps = 0.0;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (t.x[s][e] > 0.f) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+    }
+    double S[1] = {ps};
+    block_sum<TG, 1>(S, shd);
+    const double lse = M + log(S[0]);
+    const double ai = A.a[i];
+    lpart += ai * lse;
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = lse;
+    const double w = ai / S[0];
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (t.x[s][e] > 0.f) sm[c + e] += w * exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+    }
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) A.colpart[(int64_t)blockIdx.x * A.ldk + c] = sm[c];
+  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = lpart;
+}
+
+// Armijo trial in difference form (see k_armijo); v1d = em_j in float64
+template <int TG, int CH>
+__global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
+  extern __shared__ double dyn_sm[];
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float sht[TG / 32];
+  constexpr int V = 4;
+  double* sm = dyn_sm;
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
+  __syncthreads();
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  double ppsi = 0.0, plog = 0.0;
+  Tile<float, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const float mx = block_max<TG>(t.local_max(), sht);
+    const double M = (double)mx;
+    t.exp_shift(mx);
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (t.x[s][e] > 0.f) {
+          const double ev = exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+          s0 += ev;
+          s1 += ev * A.v1d[c + e];
+        }
+    }
+    double S[2] = {s0, s1};
+    block_sum<TG, 2>(S, shd);
+    const double si = S[1] / S[0];
+    const double ai = A.a[i];
+    const double l1p = log1p(si);
+    ppsi += ai * psi_log1p_minus(si);
+    plog += ai * l1p;
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = M + log(S[0]) + l1p;
+    const double w = ai / (S[0] * (1.0 + si));
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (t.x[s][e] > 0.f) {
+          const double ev = exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+          sm[c + e] += w * (ev + ev * A.v1d[c + e]);
+        }
+    }
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) A.colpart[(int64_t)blockIdx.x * A.ldk + c] = sm[c];
+  if (threadIdx.x == 0) {
+    A.rowpart[blockIdx.x * kRowParts + 0] = ppsi;
+    A.rowpart[blockIdx.x * kRowParts + 1] = plog;
+  }
+}
+
+// certificate (see k_certify): v1d = y, v2d = omega, v3d = e_c / S in float64
+template <int TG, int CH>
+__global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
+  extern __shared__ double dyn_sm[];
+  __shared__ double shd[6 * (TG / 32)];
+  __shared__ float sht[TG / 32];
+  constexpr int V = 4;
+  double* sm = dyn_sm;
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
+  __syncthreads();
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  double part[7] = {0, 0, 0, 0, 0, 0, 0};
+  Tile<float, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const float mx = block_max<TG>(t.local_max(), sht);
+    const double M = (double)mx;
+    t.exp_shift(mx);
+    const double ai = A.a[i];
+    // sweep 1: row sum; dense float64 work: zeta_i, sum C^2, sum_j C_ij e_c,j / S
+    double s0 = 0.0, zmin = kInf, c2 = 0.0, cec = 0.0;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        if (c + e >= A.n) continue;
+        if (t.x[s][e] > 0.f) s0 += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+        const double C = cost_at(A.cost, i, c + e);
+        zmin = fmin(zmin, C - A.gam[c + e]);
+        c2 += C * C;
+        cec += C * A.v3d[c + e];
+      }
+    }
+    double R[3] = {s0, c2, cec};
+    block_sum<TG, 3>(R, shd);
+    const double zeta = -block_max<TG>(-zmin, reinterpret_cast<double*>(shd + 3 * (TG / 32)));
+    const double invS0 = 1.0 / R[0];
+    // sweep 2: e_r, the plan part of the primal, complementarity, column sums
+    double pom = 0.0, psum = 0.0, pr = 0.0, cu = 0.0;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        if (c + e >= A.n || !(t.x[s][e] > 0.f)) continue;
+        const double P = exp(FFRow<TG, CH>::x64(A, i, c, e, M)) * invS0;
+        const double C = cost_at(A.cost, i, c + e);
+        const double F = ai * P * A.v1d[c + e];
+        psum += P;
+        pom += P * A.v2d[c + e];
+        pr += C * F;
+        cu += ai * P * (C - zeta - A.gam[c + e]);
+        sm[c + e] += F;
+      }
+    }
+    double Q[4] = {pom, psum, pr, cu};
+    block_sum<TG, 4>(Q, shd);
+    const double er = ai * Q[0];
+    const double rv = ai * (Q[1] - 1.0);
+    part[0] += Q[2] + er * R[2];
+    part[1] += ai * zeta;
+    part[2] += fabs(rv);
+    part[3] += er;
+    part[4] += Q[3];
+    part[5] += R[1];
+    part[6] += rv * rv;
+    if (threadIdx.x == 0) {
+      if (A.rowout != nullptr) A.rowout[i] = zeta;
+      if (A.rowout2 != nullptr) A.rowout2[i] = er;
+    }
+    if (A.plan_out != nullptr) {
+#pragma unroll
+      for (int s = 0; s < CH; ++s) {
+        const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          if (c + e >= A.n) continue;
+          const double P = t.x[s][e] > 0.f ? exp(FFRow<TG, CH>::x64(A, i, c, e, M)) * invS0 : 0.0;
+          A.plan_out[(int64_t)i * A.n + c + e] = ai * P * A.v1d[c + e] + er * A.v3d[c + e];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) A.colpart[(int64_t)blockIdx.x * A.ldk + c] = sm[c];
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 7; ++q) A.rowpart[blockIdx.x * kRowParts + q] = part[q];
+}
+
+// plan export for checks
+template <int TG, int CH>
+__global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
+  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float sht[TG / 32];
+  constexpr int V = 4;
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  Tile<float, TG, CH> t;
+  for (int i = r0; i < r1; ++i) {
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    const float mx = block_max<TG>(t.local_max(), sht);
+    const double M = (double)mx;
+    t.exp_shift(mx);
+    double ps = 0.0;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (t.x[s][e] > 0.f) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+    }
+    double S[1] = {ps};
+    block_sum<TG, 1>(S, shd);
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (c + e < A.n)
+          A.plan_out[(int64_t)i * A.n + c + e] =
+              t.x[s][e] > 0.f ? exp(FFRow<TG, CH>::x64(A, i, c, e, M)) / S[0] : 0.0;
+    }
+  }
+}
+
+}  // namespace ibsn
