@@ -223,6 +223,28 @@ int ibsn_ctx_stop_check(ibsn_ctx* ctx, double* dphi);
 int ibsn_ctx_certify(ibsn_ctx* ctx, double* primal, double* dual, double* rel_gap,
                      double* marg_viol, double* plan, double* zeta);
 
+/* ---------------------------------------------------------------------------
+ * Workspace-free plan pass.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory or pass a workspace
+ * (for example code running where another runtime owns all allocations, or a
+ * process that must keep its device footprint fixed after start-up).
+ *
+ * Computes, for the outer iterate given by (k, Gamma, gamma) exactly as
+ * ibsn_ctx_set_state does, the column sums colsum = P^k(gamma)^T a (device
+ * float64, n) of the plan of Eq. 6 and, if grad_norm is non-NULL, ||colsum - b||
+ * (host; the call then synchronises the stream).  Arithmetic is float64; the
+ * exponent is rebuilt from the cost for every entry.  Gamma and gamma are
+ * device n-vectors, either may be NULL (zero).
+ *
+ * Scratch lives in one fixed array inside the library (about 4.1 MiB on every
+ * GPU that loads it, held until the process exits); the call allocates
+ * nothing.  Limits: n <= 4096 columns (larger n returns IBSN_ERR_UNSUPPORTED),
+ * any m.  All calls share that array: calls whose kernels overlap on the GPU
+ * race, so serialise them on one stream.  The first call on each device looks
+ * up the array's device address; make it before any CUDA stream capture. */
+int ibsn_plan_pass_noalloc(const ibsn_problem* prob, int64_t k, const double* Gamma, const double* gamma,
+                           double* colsum, double* grad_norm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
