@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample")
+    ap.add_argument("--max-cg", type=int, default=0, help="CG iteration cap per Newton direction (0: library default)")
     return ap.parse_args()
 
 
@@ -223,7 +224,8 @@ def main():
     a = torch.tensor(a_np, dtype=torch.float64, device=dev)
     b = torch.tensor(b_np, dtype=torch.float64, device=dev)
     prob = G.Problem(a=a, b=b, eta=args.eta, grid=(h, h), cost_scale=scale)
-    prm = G.params(precision=args.precision, profile=1)
+    extra = {"max_cg": args.max_cg} if args.max_cg > 0 else {}
+    prm = G.params(precision=args.precision, profile=1, **extra)
     ws = G.alloc_workspace(prob, prm)
     stream = torch.cuda.current_stream(dev)
 
@@ -278,7 +280,7 @@ def main():
     # plain float64 GPU path on the same problem (speedup denominator), once
     fp64 = None
     if not args.no_fp64 and args.precision == "mixed" and rank == 0:
-        prm64 = G.params(precision="fp64", profile=1)
+        prm64 = G.params(precision="fp64", profile=1, **extra)
         ev0.record(stream)
         r64 = one(prm64)
         ev1.record(stream)

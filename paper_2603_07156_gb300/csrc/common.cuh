@@ -167,6 +167,92 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int* total) 
   return base + x - v;
 }
 
+// ---------------------------------------------------------------------------
+// Float-float arithmetic (an unevaluated sum hi + lo of two floats, ~48-bit
+// significand).  On sm_103a a dependent float64 add costs ~64 cycles against
+// ~4.5 for float32, so sums that need more than float32 accuracy are reduced
+// in this form (error-free transformations of Knuth's TwoSum and Dekker's
+// FastTwoSum) and converted to float64 once at the end.
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float err = (a - (s - bb)) + (b - bb);
+  return {s, err};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = ff_two_sum(a.hi, b.hi);
+  return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ FF ff_from(double v) {
+  const float hi = (float)v;
+  return {hi, (float)(v - (double)hi)};
+}
+__device__ __forceinline__ double ff_to(FF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF t;
+    t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = ff_add(v, t);
+  }
+  return v;
+}
+
+// Block sum of K float64 values in float-float; `sh` holds 2*K*NT/32 floats.
+template <int NT, int K>
+__device__ __forceinline__ void block_sum_ff(double (&v)[K], float* sh) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  FF f[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) f[q] = warp_sum_ff(ff_from(v[q]));
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      sh[2 * (q * NW + w)] = f[q].hi;
+      sh[2 * (q * NW + w) + 1] = f[q].lo;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    FF t = lane < NW ? FF{sh[2 * (q * NW + lane)], sh[2 * (q * NW + lane) + 1]} : FF{0.f, 0.f};
+    if constexpr (NW > 1) t = warp_sum_ff(t);
+    v[q] = ff_to(t);
+  }
+}
+
+// Block sum of K floats (float32 passes, whose accuracy is float32 anyway).
+template <int NT, int K>
+__device__ __forceinline__ void block_sum_f(float (&v)[K], float* sh) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) sh[q * NW + w] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    float t = lane < NW ? sh[q * NW + lane] : 0.f;
+    if constexpr (NW > 1) t = warp_sum(t);
+    v[q] = t;
+  }
+}
+
 // Compensated (Kahan) accumulator for float; plain for double.
 template <typename T>
 struct Acc;
@@ -197,30 +283,92 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 // Grid-wide barrier for a cooperatively launched grid (all blocks co-resident).
-// The wait is bounded: after `budget_ns` of waiting (globaltimer) the block
+// `count` only grows: every block adds 1 per barrier (release), then waits
+// (acquire loads) until the count reaches the next multiple of gridDim.x.  The
+// wait is bounded: after `budget_ns` of waiting (globaltimer) the block
 // records kDevTimeout in *err and returns false; once *err is set every later
-// call returns false at once, so all blocks leave the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* err,
+// call returns false at once, so all blocks leave the kernel.  The counter
+// must be zeroed before the launch.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* /*unused*/, int* err,
                                              unsigned long long budget_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned int* vgen = gen;
-    volatile int* verr = err;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int prev = atomicAdd(count, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
+    unsigned int old;
+    asm volatile("fence.acq_rel.gpu;\n\tatom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+    const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
+    unsigned int spins = 0;
+    unsigned long long t0 = 0;
+    for (;;) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+      if ((int)(cur - target) >= 0) break;
+      if ((++spins & 63u) == 0) {
+        if (*(volatile int*)err != 0) { ok = 0; break; }
+        const unsigned long long now = globaltimer_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > budget_ns) {
+          atomicExch(err, (int)kDevTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Grid-wide all-reduce (sum) of K float64 values per thread fused with a grid
+// barrier, two __syncthreads per call, sums in float-float: warp sums go to
+// shared memory; warp 0 forms the block partials, publishes them (st.cg),
+// arrives at the barrier (release), waits (acquire, bounded like
+// grid_barrier), sums all blocks' partials in a fixed order and broadcasts the
+// totals.  `part` holds 2 * K * gridDim.x floats, `sh` 2 * K * 32 + K doubles'
+// worth of space.  Returns false when the wait ran out (or *err was set); the
+// values in v are then unspecified.
+template <int NT, int K>
+__device__ __forceinline__ bool grid_allreduce(double (&v)[K], float2* part, unsigned int* count, int* err,
+                                               unsigned long long budget_ns, float* sh) {
+  constexpr int NW = NT / 32;
+  __shared__ int s_ok;
+  __shared__ double s_tot[K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  FF f[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) f[q] = warp_sum_ff(ff_from(v[q]));
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      sh[2 * (q * NW + w)] = f[q].hi;
+      sh[2 * (q * NW + w) + 1] = f[q].lo;
+    }
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nb = (int)gridDim.x;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      FF t = lane < NW ? FF{sh[2 * (q * NW + lane)], sh[2 * (q * NW + lane) + 1]} : FF{0.f, 0.f};
+      t = warp_sum_ff(t);
+      if (lane == 0) __stcg(part + (size_t)q * nb + blockIdx.x, make_float2(t.hi, t.lo));
+    }
+    int ok = 1;
+    if (lane == 0) {
+      unsigned int old;
+      asm volatile("fence.acq_rel.gpu;\n\tatom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+      const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
       unsigned int spins = 0;
       unsigned long long t0 = 0;
-      while (*vgen == g) {
-        if (*verr != 0) { ok = 0; break; }
-        if ((++spins & 255u) == 0) {
+      for (;;) {
+        unsigned int cur;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+        if ((int)(cur - target) >= 0) break;
+        if ((++spins & 63u) == 0) {
+          if (*(volatile int*)err != 0) { ok = 0; break; }
           const unsigned long long now = globaltimer_ns();
           if (t0 == 0) {
             t0 = now;
@@ -232,11 +380,103 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
         }
       }
     }
-    __threadfence();
-    if (*verr != 0) ok = 0;
-    s_ok = ok;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        FF t{0.f, 0.f};
+        for (int b = lane; b < nb; b += 32) {
+          const float2 pv = __ldcg(part + (size_t)q * nb + b);
+          t = ff_add(t, FF{pv.x, pv.y});
+        }
+        t = warp_sum_ff(t);
+        if (lane == 0) s_tot[q] = ff_to(t);
+      }
+    }
+    if (lane == 0) s_ok = ok;
   }
   __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = s_tot[q];
+  return s_ok != 0;
+}
+
+// grid_allreduce for float inputs (no float64 conversion on the way in): the
+// float values are summed in float-float and returned as float64 totals.
+template <int NT, int K>
+__device__ __forceinline__ bool grid_allreduce_f(const float (&vin)[K], double (&out)[K], float2* part,
+                                                 unsigned int* count, int* err, unsigned long long budget_ns,
+                                                 float* sh) {
+  constexpr int NW = NT / 32;
+  __shared__ int s_ok;
+  __shared__ double s_tot[K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  FF f[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) f[q] = warp_sum_ff(FF{vin[q], 0.f});
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      sh[2 * (q * NW + w)] = f[q].hi;
+      sh[2 * (q * NW + w) + 1] = f[q].lo;
+    }
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nb = (int)gridDim.x;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      FF t = lane < NW ? FF{sh[2 * (q * NW + lane)], sh[2 * (q * NW + lane) + 1]} : FF{0.f, 0.f};
+      t = warp_sum_ff(t);
+      if (lane == 0) __stcg(part + (size_t)q * nb + blockIdx.x, make_float2(t.hi, t.lo));
+    }
+    int ok = 1;
+    if (lane == 0) {
+      unsigned int old;
+      asm volatile("fence.acq_rel.gpu;\n\tatom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+      const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
+      unsigned int spins = 0;
+      unsigned long long t0 = 0;
+      for (;;) {
+        unsigned int cur;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+        if ((int)(cur - target) >= 0) break;
+        if ((++spins & 63u) == 0) {
+          if (*(volatile int*)err != 0) { ok = 0; break; }
+          const unsigned long long now = globaltimer_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if (now - t0 > budget_ns) {
+            atomicExch(err, (int)kDevTimeout);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+      FF t[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) t[q] = FF{0.f, 0.f};
+      for (int b = lane; b < nb; b += 32) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const float2 pv = __ldcg(part + (size_t)q * nb + b);
+          t[q] = ff_add(t[q], FF{pv.x, pv.y});
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        t[q] = warp_sum_ff(t[q]);
+        if (lane == 0) s_tot[q] = ff_to(t[q]);
+      }
+    }
+    if (lane == 0) s_ok = ok;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = s_tot[q];
   return s_ok != 0;
 }
 

@@ -27,6 +27,7 @@ struct DenseArgs {
   const T* v2;         // per-column input 2
   const T* v3;         // per-column input 3
   const double* a;     // m
+  const T* aT;         // m, a in the pass precision
   double* rowout;      // m, variant specific (lse, e_r, zeta)
   double* rowout2;     // m
   double* colpart;     // gridDim.x x ldk
@@ -169,6 +170,32 @@ __device__ __forceinline__ void row_range(int m, int rpb, int& r0, int& r1) {
   r1 = min(m, r0 + rpb);
 }
 
+// Shift subtracted from a row's exponents before exp.  Float32 passes use 0:
+// the anchored K is <= 0 with row maximum 0, the potential offsets d stay
+// within [-16, 16] (the anchor is rebuilt beyond that) and an Armijo trial
+// adds at most 60, so exp of every row maximum lies in [e^-76, e^76] and
+// neither overflows a float row sum nor underflows the whole row.  Float64
+// passes reduce the row maximum.
+template <typename T, int TG, int CH>
+__device__ __forceinline__ T row_shift(const Tile<T, TG, CH>& t, T* sht) {
+  if constexpr (std::is_same<T, float>::value) {
+    return 0.f;
+  } else {
+    return block_max<TG>(t.local_max(), sht);
+  }
+}
+
+// Block sum of K per-thread sums: float32 in float32 passes (their accuracy is
+// float32 anyway), float-float in float64 passes.  `shf` holds 8 * TG/32 floats.
+template <typename T, int TG, int K>
+__device__ __forceinline__ void row_sum(T (&v)[K], float* shf) {
+  if constexpr (std::is_same<T, float>::value) {
+    block_sum_f<TG, K>(v, shf);
+  } else {
+    block_sum_ff<TG, K>(v, shf);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Plan pass (Eqs. 6-7): lse_i, c_j = sum_i a_i P_ij, sum_i a_i lse_i.
 // rowout = lse (nullable).
@@ -176,32 +203,32 @@ __device__ __forceinline__ void row_range(int m, int rpb, int& r0, int& r1) {
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
   extern __shared__ double dyn_sm[];
-  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   ColAcc<T, TG, CH> acc;
   acc.init(dyn_sm, A.ldk);
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
-  double lpart = 0.0;
+  T lpart = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
-    const T mx = block_max<TG>(t.local_max(), sht);
-    double S[1] = {(double)t.exp_shift(mx)};
-    block_sum<TG, 1>(S, shd);
-    const double lse = (double)mx + log(S[0]);
-    const double ai = A.a[i];
+    const T mx = row_shift<T, TG, CH>(t, sht);
+    T S[1] = {t.exp_shift(mx)};
+    row_sum<T, TG, 1>(S, shf);
+    const T ai = A.aT[i];
+    const T lse = mx + log(S[0]);
     lpart += ai * lse;
-    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = lse;
-    const T w = (T)(ai / S[0]);
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = (double)lse;
+    const T w = ai / S[0];
 #pragma unroll
     for (int s = 0; s < CH; ++s)
 #pragma unroll
       for (int e = 0; e < V; ++e) acc.add(s, e, w * t.x[s][e]);
   }
   acc.flush(A.colpart + (int64_t)blockIdx.x * A.ldk, A.ldk);
-  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = lpart;
+  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = (double)lpart;
 }
 
 // ---------------------------------------------------------------------------
@@ -219,23 +246,32 @@ __device__ __forceinline__ double psi_log1p_minus(double s) {
   }
   return log1p(s) - s;
 }
+__device__ __forceinline__ float psi_log1p_minus(float s) {
+  // float: series sum_{k>=2} (-1)^(k+1) s^k / k to s^10 for |s| < 0.1
+  if (fabsf(s) < 0.1f) {
+    const float s2 = s * s;
+    return s2 * (-0.5f + s * (1.f / 3.f + s * (-0.25f + s * (0.2f + s * (-1.f / 6.f + s * (1.f / 7.f + s * (
+                     -0.125f + s * (1.f / 9.f + s * -0.1f))))))));
+  }
+  return log1pf(s) - s;
+}
 
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
   extern __shared__ double dyn_sm[];
-  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   ColAcc<T, TG, CH> acc;
   acc.init(dyn_sm, A.ldk);
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
-  double ppsi = 0.0, plog = 0.0;
+  T ppsi = T(0), plog = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
-    const T mx = block_max<TG>(t.local_max(), sht);
-    T s1 = T(0), s0 = T(0);
+    const T mx = row_shift<T, TG, CH>(t, sht);
+    T S[2] = {T(0), T(0)};
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
@@ -250,19 +286,18 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
       for (int e = 0; e < V; ++e) {
         const T ev = exp_t(t.x[s][e] - mx);
         t.x[s][e] = ev;
-        s0 += ev;
-        s1 += ev * em[e];
+        S[0] += ev;
+        S[1] += ev * em[e];
       }
     }
-    double S[2] = {(double)s0, (double)s1};
-    block_sum<TG, 2>(S, shd);
-    const double si = S[1] / S[0];
-    const double ai = A.a[i];
-    const double l1p = log1p(si);
+    row_sum<T, TG, 2>(S, shf);
+    const T si = S[1] / S[0];
+    const T ai = A.aT[i];
+    const T l1p = log1p(si);
     ppsi += ai * psi_log1p_minus(si);
     plog += ai * l1p;
-    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = (double)mx + log(S[0]) + l1p;
-    const T w = (T)(ai / (S[0] * (1.0 + si)));
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = (double)(mx + log(S[0]) + l1p);
+    const T w = ai / (S[0] * (T(1) + si));
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
@@ -279,8 +314,8 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
   }
   acc.flush(A.colpart + (int64_t)blockIdx.x * A.ldk, A.ldk);
   if (threadIdx.x == 0) {
-    A.rowpart[blockIdx.x * kRowParts + 0] = ppsi;
-    A.rowpart[blockIdx.x * kRowParts + 1] = plog;
+    A.rowpart[blockIdx.x * kRowParts + 0] = (double)ppsi;
+    A.rowpart[blockIdx.x * kRowParts + 1] = (double)plog;
   }
 }
 
@@ -304,21 +339,19 @@ __device__ __forceinline__ T h_of_1pu(T u) {
 
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
-  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
-  const double invS = A.s1 > 0.0 ? 1.0 / A.s1 : 0.0;
-  double dpart = 0.0;
+  const T invS = (T)(A.s1 > 0.0 ? 1.0 / A.s1 : 0.0);
+  T dpart = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
-    const T mx = block_max<TG>(t.local_max(), sht);
-    double S[1] = {(double)t.exp_shift(mx)};
-    block_sum<TG, 1>(S, shd);
-    const T invS0 = (T)(1.0 / S[0]);
-    T po = T(0);
+    const T mx = row_shift<T, TG, CH>(t, sht);
+    // row sum and sum_j e_ij omega_j in one reduction
+    T R[2] = {t.exp_shift(mx), T(0)};
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
@@ -326,18 +359,17 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
         T om[V];
         load_vec(A.v1 + c, om);
 #pragma unroll
-        for (int e = 0; e < V; ++e) po += t.x[s][e] * invS0 * om[e];
+        for (int e = 0; e < V; ++e) R[1] += t.x[s][e] * om[e];
       }
     }
-    double R[1] = {(double)po};
-    block_sum<TG, 1>(R, shd);
-    const double ai = A.a[i];
-    const double er = ai * R[0];
-    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = er;
-    const T ai_t = (T)ai;
-    const T logai_m = (T)(log(ai) - (double)mx - log(S[0]));  // log X_ij = x_ij + this
-    const T erS = (T)(er * invS);
-    T dl = T(0);
+    row_sum<T, TG, 2>(R, shf);
+    const T invS0 = T(1) / R[0];
+    const T ai = A.aT[i];
+    const T er = ai * R[1] * invS0;
+    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = (double)er;
+    const T logai_m = log(ai) - mx - log(R[0]);  // log X_ij = x_ij + this
+    const T erS = er * invS;
+    T D[1] = {T(0)};
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
@@ -349,29 +381,28 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
         for (int e = 0; e < V; ++e) {
           if (c + e >= A.n) continue;
           // Xhat = X y + extra, X = a_i P_ij, extra = e_r,i e_c,j / S
-          const T X = ai_t * (t.x[s][e] * invS0);
+          const T X = ai * (t.x[s][e] * invS0);
           const T extra = erS * ec[e];
           const T xh = X * (T(1) - om[e]) + extra;
           if (xh <= T(0)) {
-            dl += X;                                   // 0 log 0 - 0 + X
+            D[0] += X;                                   // 0 log 0 - 0 + X
           } else if (extra <= X) {
-            dl += X * h_of_1pu(extra / X - om[e]);     // |u| <= 1: no overflow
+            D[0] += X * h_of_1pu(extra / X - om[e]);     // |u| <= 1: no overflow
           } else {
             // extra mass on a cell with tiny X: log X from the exponent
             T kv[V], d[V];
             load_vec(A.K + (int64_t)i * A.ldk + c, kv);
             load_vec(A.dv + c, d);
             const T logX = kv[e] + d[e] + logai_m;
-            dl += xh * (log(xh) - logX) - xh + X;
+            D[0] += xh * (log(xh) - logX) - xh + X;
           }
         }
       }
     }
-    double D[1] = {(double)dl};
-    block_sum<TG, 1>(D, shd);
+    row_sum<T, TG, 1>(D, shf);
     dpart += D[0];
   }
-  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = dpart;
+  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = (double)dpart;
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +412,7 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
 // ---------------------------------------------------------------------------
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
-  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   __shared__ int shi[TG / 32];
   __shared__ unsigned long long s_base;
@@ -397,10 +428,10 @@ __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
-    const T mx = block_max<TG>(t.local_max(), sht);
-    double S[1] = {(double)t.exp_shift(mx)};
-    block_sum<TG, 1>(S, shd);
-    const T invS0 = (T)(1.0 / S[0]);
+    const T mx = row_shift<T, TG, CH>(t, sht);
+    T S[1] = {t.exp_shift(mx)};
+    row_sum<T, TG, 1>(S, shf);
+    const T invS0 = T(1) / S[0];
     if (i == A.istar) {
 #pragma unroll
       for (int s = 0; s < CH; ++s) {
@@ -431,8 +462,8 @@ __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
         }
       }
     }
-    double KS[1] = {(double)ks};
-    block_sum<TG, 1>(KS, shd);
+    T KS[1] = {ks};
+    row_sum<T, TG, 1>(KS, shf);
     int total = 0;
     const int off = block_exclusive_scan<TG>(kc, shi, &total);
     if (threadIdx.x == 0) {
@@ -445,7 +476,7 @@ __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
     __syncthreads();
     const unsigned long long base = s_base;
     if ((long long)(base + total) > A.cap) continue;
-    const T inv_ks = (T)(1.0 / KS[0]);
+    const T inv_ks = T(1) / KS[0];
     int64_t pos = (int64_t)base + off;
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
@@ -496,6 +527,7 @@ template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
   extern __shared__ double dyn_sm[];
   __shared__ double shd[6 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   ColAcc<T, TG, CH> acc;
@@ -506,9 +538,9 @@ __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
-    const T mx = block_max<TG>(t.local_max(), sht);
+    const T mx = row_shift<T, TG, CH>(t, sht);
     double S[1] = {(double)t.exp_shift(mx)};
-    block_sum<TG, 1>(S, shd);
+    block_sum_ff<TG, 1>(S, shf);
     const double invS0 = 1.0 / S[0];
     const double ai = A.a[i];
     // sweep 1: P row sum, sum P omega, zeta_i = min_j C_ij - gamma_j, sum C^2
@@ -532,7 +564,7 @@ __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
       }
     }
     double R[3] = {psum, pom, c2};
-    block_sum<TG, 3>(R, shd);
+    block_sum_ff<TG, 3>(R, shf);
     const double zeta = -block_max<TG>(-zmin, reinterpret_cast<double*>(shd + 3 * (TG / 32)));
     const double er = ai * R[1];
     // sweep 2: primal and complementarity
@@ -559,7 +591,7 @@ __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
       }
     }
     double Q[2] = {pr, cu};
-    block_sum<TG, 2>(Q, shd);
+    block_sum_ff<TG, 2>(Q, shf);
     const double rv = ai * (R[0] - 1.0);
     part[0] += Q[0];
     part[1] += ai * zeta;
@@ -636,7 +668,7 @@ __global__ void __launch_bounds__(TG) k_reanchor(DenseArgs<T> A) {
 // ---------------------------------------------------------------------------
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
-  __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   int r0, r1;
@@ -644,10 +676,10 @@ __global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
-    const T mx = block_max<TG>(t.local_max(), sht);
-    double S[1] = {(double)t.exp_shift(mx)};
-    block_sum<TG, 1>(S, shd);
-    const T invS0 = (T)(1.0 / S[0]);
+    const T mx = row_shift<T, TG, CH>(t, sht);
+    T S[1] = {t.exp_shift(mx)};
+    row_sum<T, TG, 1>(S, shf);
+    const T invS0 = T(1) / S[0];
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
@@ -682,6 +714,7 @@ template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
   extern __shared__ double dyn_sm[];
   __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
   double* sm = dyn_sm;
@@ -705,7 +738,7 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
         if (t.x[s][e] > 0.f) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
     }
     double S[1] = {ps};
-    block_sum<TG, 1>(S, shd);
+    block_sum_ff<TG, 1>(S, shf);
     const double lse = M + log(S[0]);
     const double ai = A.a[i];
     lpart += ai * lse;
@@ -729,6 +762,7 @@ template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
   extern __shared__ double dyn_sm[];
   __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
   double* sm = dyn_sm;
@@ -756,7 +790,7 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
         }
     }
     double S[2] = {s0, s1};
-    block_sum<TG, 2>(S, shd);
+    block_sum_ff<TG, 2>(S, shf);
     const double si = S[1] / S[0];
     const double ai = A.a[i];
     const double l1p = log1p(si);
@@ -788,6 +822,7 @@ template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   extern __shared__ double dyn_sm[];
   __shared__ double shd[6 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
   double* sm = dyn_sm;
@@ -819,8 +854,8 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
       }
     }
     double R[3] = {s0, c2, cec};
-    block_sum<TG, 3>(R, shd);
-    const double zeta = -block_max<TG>(-zmin, reinterpret_cast<double*>(shd + 3 * (TG / 32)));
+    block_sum_ff<TG, 3>(R, shf);
+    const double zeta = -block_max<TG>(-zmin, shd);
     const double invS0 = 1.0 / R[0];
     // sweep 2: e_r, the plan part of the primal, complementarity, column sums
     double pom = 0.0, psum = 0.0, pr = 0.0, cu = 0.0;
@@ -841,7 +876,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
       }
     }
     double Q[4] = {pom, psum, pr, cu};
-    block_sum<TG, 4>(Q, shd);
+    block_sum_ff<TG, 4>(Q, shf);
     const double er = ai * Q[0];
     const double rv = ai * (Q[1] - 1.0);
     part[0] += Q[2] + er * R[2];
@@ -878,6 +913,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
   __shared__ double shd[2 * (TG / 32)];
+  __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
   int r0, r1;
@@ -897,7 +933,7 @@ __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
         if (t.x[s][e] > 0.f) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
     }
     double S[1] = {ps};
-    block_sum<TG, 1>(S, shd);
+    block_sum_ff<TG, 1>(S, shf);
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<float, TG, CH>::col(s);

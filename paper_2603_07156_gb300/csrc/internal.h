@@ -74,6 +74,7 @@ enum Slot : int {
   S_CBAD = 25,     // C check: count of negative or non-finite entries
   S_CG_ITERS = 26, S_CG_RES = 27,
   S_NNZ = 28,
+  S_MAXROW = 29, S_MAXCOL = 30,  // longest row / column of P_rho (diagnostics)
   S_NSLOTS = 64
 };
 
@@ -137,15 +138,19 @@ cudaError_t launch_export_sparse(const SparseBufs& S, int m, int64_t n, int ista
                                  cudaStream_t st);
 
 struct PcgBufs {
-  double *x, *r, *z, *p, *q, *w, *rhs;
-  double* part;         // 4 x maxblocks
+  double *x, *p, *rhs;  // n
+  double* cs;           // 4n: packed column state {r, w, s, 1/diag}
+  float* cs32;          // 4n floats: float copy of the packed state
+  double* t;            // m (float or double values)
+  double* part;         // 8 x maxblocks (float-float partials of 6 sums)
   unsigned int* bar;    // [count, gen]
   int* err;
 };
 
 cudaError_t launch_pcg(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, int istar, bool fp64,
-                       const double* a, double eta, double shift, double rtol, int maxit,
-                       double timeout_s, int nsm, double* scal, cudaStream_t st);
+                       const double* a, const float* a32, double eta, double shift, double rtol, int maxit,
+                       double timeout_s, int nsm, int64_t nnz, double* scal, cudaStream_t st);
 int pcg_max_blocks(int nsm);
+cudaError_t launch_len_stats(const SparseBufs& S, int m, int64_t n, double* scal, cudaStream_t st);
 
 }  // namespace ibsn

@@ -46,6 +46,10 @@ __global__ void k_log(int64_t n, const double* x, double* y) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) y[j] = log(x[j]);
 }
+__global__ void k_to_float(int64_t n, const double* x, float* y) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) y[j] = (float)x[j];
+}
 __global__ void k_axpy(int64_t n, double alpha, const double* x, double* y) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) y[j] += alpha * x[j];
@@ -144,7 +148,7 @@ struct ibsn_ctx {
   double* K64 = nullptr;    // float64 anchored matrix (plain float64 mode)
   double *Gam, *gam, *ganc, *dd, *c, *c2, *g, *delta, *logb, *wv, *colF;
   double *lse, *lse2, *er, *zeta;
-  float *d32, *em32;
+  float *d32, *em32, *a32;
   double *d64, *em64;
   RoundVecs rv{};
   double *colpart, *rowpart, *blockbuf;
@@ -219,6 +223,7 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   for (double** v : nvec) *v = cv.take<double>(n);
   double** mvec[] = {&X->lse, &X->lse2, &X->er, &X->zeta};
   for (double** v : mvec) *v = cv.take<double>(m);
+  X->a32 = cv.take<float>(m);
   float** fvec[] = {&X->d32, &X->em32, &X->rv.y32, &X->rv.om32, &X->rv.ec32, &X->rv.ecs32};
   for (float** v : fvec) *v = cv.take<float>(ldk);
   double** dvec[] = {&X->d64, &X->em64, &X->rv.y64, &X->rv.om64, &X->rv.ec64, &X->rv.ecs64};
@@ -239,10 +244,12 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   X->sp.crho = cv.take<double>(n);
   X->sp.diag = cv.take<double>(n);
   X->sp.cap = cap;
-  double** pvec[] = {&X->pc.x, &X->pc.r, &X->pc.z, &X->pc.p, &X->pc.q, &X->pc.rhs};
+  double** pvec[] = {&X->pc.x, &X->pc.p, &X->pc.rhs};
   for (double** v : pvec) *v = cv.take<double>(n);
-  X->pc.w = cv.take<double>(m);
-  X->pc.part = cv.take<double>(4 * (size_t)pcg_max_blocks(nsm));
+  X->pc.cs = cv.take<double>(4 * (size_t)n);
+  X->pc.cs32 = cv.take<float>(4 * (size_t)n);
+  X->pc.t = cv.take<double>(m);
+  X->pc.part = cv.take<double>(8 * (size_t)pcg_max_blocks(nsm));
   X->pc.bar = cv.take<unsigned int>(4);
   X->pc.err = cv.take<int>(4);
   X->scal = cv.take<double>(S_NSLOTS);
@@ -332,6 +339,11 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
     A.v1 = in.v1d;
     A.v2 = in.v2d;
     A.v3 = in.v3d;
+  }
+  if constexpr (F) {
+    A.aT = X->a32;
+  } else {
+    A.aT = X->a;
   }
   A.Klo = X->Klo;
   A.dv64 = X->d64;
@@ -504,8 +516,8 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
   const bool prof0 = X->prof.on;
   {
     ProfScope ps(X, 6, 0.0, X->sp_f64);
-    CK(launch_pcg(S, X->pc, X->m, X->n, X->istar, X->sp_f64, X->a, X->eta, shift, rtol, max_cg,
-                  X->prm.wait_timeout_s, X->nsm, X->scal, X->st));
+    CK(launch_pcg(S, X->pc, X->m, X->n, X->istar, X->sp_f64, X->a, X->a32, X->eta, shift, rtol, max_cg,
+                  X->prm.wait_timeout_s, X->nsm, X->nnz, X->scal, X->st));
   }
   int perr = 0;
   CK(cudaMemcpyAsync(&perr, X->pc.err, sizeof(int), cudaMemcpyDeviceToHost, X->st));
@@ -698,7 +710,8 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   X->anorm = std::sqrt(X->anorm);
   X->bnorm = std::sqrt(X->bnorm);
   k_log<<<(unsigned)((X->n + 255) / 256), 256, 0, st>>>(X->n, pr->b, X->logb);
-  note_launch();
+  k_to_float<<<(unsigned)((X->m + 255) / 256), 256, 0, st>>>(X->m, pr->a, X->a32);
+  note_launch(2);
   // zero state, pad the float/double per-column vectors
   cudaMemsetAsync(X->Gam, 0, sizeof(double) * X->n, st);
   cudaMemsetAsync(X->gam, 0, sizeof(double) * X->n, st);
@@ -958,8 +971,12 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
       if (X->prec != 0) rtol = std::max(rtol, P.cg_rtol_floor_mixed);  // float32 Hessian values
       int cgit = 0;
       double cgres = 0.0;
+      if (P.verbose > 1) CK(launch_len_stats(X->sp, X->m, X->n, X->scal, X->st));
       RT(do_direction(X, gn, rtol, P.max_cg, &cgit, &cgres));
       tot_cg += cgit;
+      if (P.verbose > 1)
+        fprintf(stderr, "[ibsn]   newton k=%d v=%d |g|=%.3e nnz=%lld maxrow=%d maxcol=%d cg=%d rtol=%.1e\n", k, v, gn,
+                (long long)X->nnz, (int)X->h_scal[S_MAXROW], (int)X->h_scal[S_MAXCOL], cgit, rtol);
       // trials whose largest exponent change t max|Delta|/eta exceeds the pass
       // range are rejected unevaluated (exp would overflow in that precision)
       const double dmax = X->h_scal[S_DELTAMAX];
@@ -999,8 +1016,10 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
       gn_prev = gn;
     }
     (void)gn_prev;
-    // certificate at X^{k+1} = diag(a) P^k(gamma^{k,fin})
-    RT(do_certify(X, &cert, nullptr, nullptr));
+    // certificate at X^{k+1} = diag(a) P^k(gamma^{k,fin}); with float32 passes
+    // it only steers the switch to the polish, so it is taken every 4th step
+    const bool certify_now = X->prec != 1 || (k % 4) == 0 || k + 1 == P.max_outer;
+    if (certify_now) RT(do_certify(X, &cert, nullptr, nullptr));
     if (!std::isfinite(cert.gap)) return IBSN_ERR_NUMERICAL;
     if (X->prec == 2) ++polish_outer;
     if (P.verbose)
@@ -1018,17 +1037,17 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
       break;
     }
     // mixed precision: float32 passes until the (float32-plan) certificate
-    // reaches polish_gap, or makes no 2x progress over 50 outer steps; then
-    // float64 passes to the end
+    // reaches polish_gap, or makes no 2x progress over 12 outer steps (the
+    // float32 noise floor of the certificate); then float-float passes
     int next_prec = X->prec;
-    if (X->prec == 1 && P.polish) {
+    if (X->prec == 1 && P.polish && certify_now) {
       if (cert.gap < 0.5 * best_gap) {
         best_gap = cert.gap;
         stall = 0;
       } else {
-        ++stall;
+        stall += 4;
       }
-      if (cert.gap <= P.polish_gap || stall >= 50) next_prec = 2;
+      if (cert.gap <= P.polish_gap || stall >= 12) next_prec = 2;
     }
     if (k + 1 < P.max_outer) RT(outer_advance(X, next_prec));
   }

@@ -7,6 +7,8 @@
 // deterministically: block b of the sparsify pass owns rows [b*rpb, (b+1)*rpb),
 // its per-column counts are prefix-summed over blocks, and each block scatters
 // its rows in row order.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -121,15 +123,17 @@ __global__ void k_export_sparse(const int32_t* __restrict__ pool_col, const T* _
 }
 
 // ---------------------------------------------------------------------------
-// Persistent PCG.  Three bounded grid barriers per iteration:
-//   A rows:  u_i = sum_j P_ij p_j with p = z + beta p_old formed on the fly,
-//            w_i = a_i u_i; row i* (dense) as per-block partial dots
-//   B cols:  p_j <- z_j + beta p_j; v_j = sum_i P_ij w_i + P_i*j w_i*;
-//            q_j = (c_rho_j p_j - v_j)/eta + shift p_j; partial p.q
-//   C upd:   alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag;
-//            partials r.z and r.r
-// Every block reduces the per-block partials itself in a fixed order, so all
-// blocks take the same branch.
+// Persistent preconditioned CG in the Chronopoulos-Gear arrangement: both
+// inner products of an iteration are formed after its single operator
+// application, so an iteration needs two grid barriers:
+//   R (rows):  t_i = a_i sum_j P_ij u_j, u = M^{-1} r formed on the fly from the
+//              packed column state; row i* (dense) as per-block partial dots
+//   C (cols):  s = w + beta s, p = u + beta p, x += alpha p, r -= alpha s,
+//              u = M^{-1} r, w = A u with A = (diag(c_rho) - P^T diag(a) P)/eta
+//              + shift I; partials of (r,u), (w,u), (r,r)
+// Rows and columns are handled by groups of G lanes; each lane keeps up to E
+// entries of its row and of its column in registers for the whole solve, the
+// rest is streamed.  Column state is packed per column as {r, w} {s, 1/diag}.
 // ---------------------------------------------------------------------------
 constexpr int kPcgThreads = 512;
 
@@ -147,8 +151,12 @@ struct PcgArgs {
   const double* crho;
   const double* diag;
   const double* rhs;
-  double *x, *r, *z, *p, *q, *w;
-  double* part;  // [4][nb]
+  double* x;
+  double* p;
+  double2* cs;   // 2n: [2j] = {r_j, w_j}, [2j+1] = {s_j, 1/diag_j}
+  float4* cs32;  // n: float copy {r, w, s, 1/diag} gathered by the float32 row phase
+  T* t;          // m
+  float2* part;  // [6][nb] float-float block partials
   unsigned int* bar;
   int* err;
   double* scal;
@@ -156,151 +164,416 @@ struct PcgArgs {
   int64_t n;
   double inv_eta, shift, rtol;
   int maxit;
-  unsigned long long deadline_ns;
+  unsigned long long budget_ns;
 };
 
-__device__ __forceinline__ double reduce_parts(const double* part, int nb) {
-  // fixed-order reduction of nb partials by warp 0, broadcast through smem
-  __shared__ double s_val;
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int q = threadIdx.x; q < nb; q += 32) s += __ldcg(part + q);
-    s = warp_sum(s);
-    if (threadIdx.x == 0) s_val = s;
-  }
-  __syncthreads();
-  const double v = s_val;
-  __syncthreads();
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <int NT>
-__device__ __forceinline__ double block_total(double v, double* sh) {
-  double t[1] = {v};
-  block_sum<NT, 1>(t, sh);
-  return t[0];
+// u_j = (r_j - alpha (w_j + beta s_j)) / diag_j from the packed state
+__device__ __forceinline__ double u_from(const double2* cs, int64_t j, double alpha, double beta) {
+  const double2 rw = __ldcg(cs + 2 * j);
+  const double2 sd = __ldcg(cs + 2 * j + 1);
+  return (rw.x - alpha * (rw.y + beta * sd.x)) * sd.y;
+}
+// the same from the float copy (float32 Hessian: the product needs no more)
+__device__ __forceinline__ float u_from32(const float4* cs, int64_t j, float alpha, float beta) {
+  const float4 c = __ldcg(cs + j);
+  return (c.x - alpha * (c.y + beta * c.z)) * c.w;
+}
+template <typename T>
+__device__ __forceinline__ T u_at(const double2* cs, const float4* cs32, int64_t j, double alpha, double beta,
+                                  float alpha32, float beta32) {
+  if constexpr (std::is_same<T, float>::value) {
+    return u_from32(cs32, j, alpha32, beta32);
+  } else {
+    return u_from(cs, j, alpha, beta);
+  }
+}
+template <int G, typename V>
+__device__ __forceinline__ V group_sum_t(V v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kPcgThreads) k_pcg(PcgArgs<T> A) {
-  __shared__ double sh[2 * (kPcgThreads / 32)];
+template <typename T, int G, int E>
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(PcgArgs<T> A) {
+  __shared__ float sh[2 * 6 * 32];
   const int nb = gridDim.x;
-  const int lane = threadIdx.x & 31;
-  const int nwb = kPcgThreads / 32;
-  const int gwarp = blockIdx.x * nwb + (threadIdx.x >> 5);
-  const int nwarps = nb * nwb;
+  const int gl = threadIdx.x & (G - 1);
+  const int gid = (int)(((int64_t)blockIdx.x * kPcgThreads + threadIdx.x) / G);
+  const int ngroups = nb * (kPcgThreads / G);
   const int64_t gtid = (int64_t)blockIdx.x * kPcgThreads + threadIdx.x;
   const int64_t nthr = (int64_t)nb * kPcgThreads;
-  double* partRZ = A.part;
-  double* partRR = A.part + nb;
-  double* partPQ = A.part + 2 * nb;
-  double* partD = A.part + 3 * nb;
-  unsigned int* bcount = A.bar;
-  unsigned int* bgen = A.bar + 1;
 
-  // init: x = 0, r = rhs, z = r / diag
-  double lrz = 0.0, lrr = 0.0;
+  // registers: the first row and the first column of this group
+  const int i0 = gid;
+  int r_len = 0;
+  int64_t r_start = 0;
+  int r_col[E];
+  T r_val[E];
+  if (i0 < A.m && i0 != A.istar) {
+    r_start = A.row_start[i0];
+    r_len = A.row_len[i0];
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = gl + e * G;
+    r_col[e] = k < r_len ? A.col[r_start + k] : 0;
+    r_val[e] = k < r_len ? A.val[r_start + k] : T(0);
+  }
+  const int64_t j0 = gid;
+  int64_t c_start = 0;
+  int c_len = 0;
+  int c_row[E];
+  T c_val[E];
+  if (j0 < A.n) {
+    c_start = A.colptr[j0];
+    c_len = (int)(A.colptr[j0 + 1] - c_start);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = gl + e * G;
+    c_row[e] = k < c_len ? A.crow[c_start + k] : 0;
+    c_val[e] = k < c_len ? A.cval[c_start + k] : T(0);
+  }
+
+  // state: r = rhs, w = 0, s = 0, p = 0, x = 0.  Row i* of P_rho (dense, q)
+  // enters H u through the scalar q^T u; for the next u = (r - alpha (w +
+  // beta s)) / diag it is Qr - alpha (Qw + beta Qs) with Qv = sum_j q_j v_j / diag_j
+  // over the stored state, so those three sums ride along with the CG dots.
+  constexpr bool F32 = std::is_same<T, float>::value;
+  double red[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int64_t j = gtid; j < A.n; j += nthr) {
-    const double rj = A.rhs[j];
-    const double zj = rj / A.diag[j];
-    __stcg(A.x + j, 0.0);
-    __stcg(A.r + j, rj);
-    __stcg(A.z + j, zj);
+    const double dinv = 1.0 / A.diag[j];
+    __stcg(A.cs + 2 * j, make_double2(A.rhs[j], 0.0));
+    __stcg(A.cs + 2 * j + 1, make_double2(0.0, dinv));
+    if constexpr (F32) __stcg(A.cs32 + j, make_float4((float)A.rhs[j], 0.f, 0.f, (float)dinv));
     __stcg(A.p + j, 0.0);
-    lrz += rj * zj;
-    lrr += rj * rj;
+    __stcg(A.x + j, 0.0);
+    red[3] += (double)A.prow[j] * dinv * A.rhs[j];
   }
-  {
-    double t[2] = {lrz, lrr};
-    block_sum<kPcgThreads, 2>(t, sh);
-    if (threadIdx.x == 0) {
-      __stcg(partRZ + blockIdx.x, t[0]);
-      __stcg(partRR + blockIdx.x, t[1]);
-    }
-  }
-  if (!grid_barrier(bcount, bgen, A.err, A.deadline_ns)) return;
+  if (!grid_allreduce<kPcgThreads, 6>(red, A.part, A.bar, A.err, A.budget_ns, sh)) return;
+  double Qr = red[3], Qw = 0.0, Qs = 0.0;
 
-  double rz_old = 0.0, bnorm = 0.0, rr = 0.0;
+  double alpha = 0.0, beta = 0.0, gam = 0.0, bnorm = 0.0, rr = 0.0;
+  bool warm = true;
   int it = 0;
-  // column slice of row i* owned by this block
-  const int64_t dchunk = (A.n + nb - 1) / nb;
-  const int64_t d0 = (int64_t)blockIdx.x * dchunk;
-  const int64_t d1 = d0 + dchunk < A.n ? d0 + dchunk : A.n;
   for (;;) {
-    const double rz = reduce_parts(partRZ, nb);
-    rr = reduce_parts(partRR, nb);
-    if (it == 0) bnorm = sqrt(rr);
-    if (bnorm == 0.0 || sqrt(rr) <= A.rtol * bnorm || it >= A.maxit) break;
-    const double beta = (it == 0) ? 0.0 : rz / rz_old;
-    rz_old = rz;
-    // ---- A: rows
-    for (int i = gwarp; i < A.m; i += nwarps) {
-      if (i == A.istar) continue;
-      const int64_t s = A.row_start[i];
-      const int len = A.row_len[i];
-      double acc = 0.0;
-      for (int k = lane; k < len; k += 32) {
-        const int32_t j = A.col[s + k];
-        acc += (double)A.val[s + k] * (__ldcg(A.z + j) + beta * __ldcg(A.p + j));
+    // ---- R: t = a o (P u); the trip count is uniform so group shuffles never diverge
+    const float alpha32 = (float)alpha, beta32 = (float)beta;
+    const int qr = (A.m + ngroups - 1) / ngroups;
+    for (int q = 0; q < qr; ++q) {
+      const int i = i0 + q * ngroups;
+      T acc = T(0);
+      if (i < A.m && i != A.istar) {
+        if (q == 0) {
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            if (gl + e * G < r_len) acc += r_val[e] * u_at<T>(A.cs, A.cs32, r_col[e], alpha, beta, alpha32, beta32);
+          for (int k = gl + E * G; k < r_len; k += G)
+            acc += A.val[r_start + k] * u_at<T>(A.cs, A.cs32, A.col[r_start + k], alpha, beta, alpha32, beta32);
+        } else {
+          const int64_t st = A.row_start[i];
+          const int ln = A.row_len[i];
+          for (int k = gl; k < ln; k += G)
+            acc += A.val[st + k] * u_at<T>(A.cs, A.cs32, A.col[st + k], alpha, beta, alpha32, beta32);
+        }
       }
-      acc = warp_sum(acc);
-      if (lane == 0) __stcg(A.w + i, A.a[i] * acc);
+      acc = group_sum_t<G>(acc);
+      if (gl == 0 && i < A.m && i != A.istar) __stcg(A.t + i, (T)(A.a[i] * (double)acc));
     }
-    {
-      double ld = 0.0;
-      for (int64_t j = d0 + threadIdx.x; j < d1; j += kPcgThreads)
-        ld += (double)A.prow[j] * (__ldcg(A.z + j) + beta * __ldcg(A.p + j));
-      ld = block_total<kPcgThreads>(ld, sh);
-      if (threadIdx.x == 0) __stcg(partD + blockIdx.x, ld);
-    }
-    if (!grid_barrier(bcount, bgen, A.err, A.deadline_ns)) return;
-    // ---- B: columns
-    const double wstar = A.a[A.istar] * reduce_parts(partD, nb);
-    double lpq = 0.0;
-    for (int64_t j = gwarp; j < A.n; j += nwarps) {
-      double acc = 0.0;
-      const int64_t k1 = A.colptr[j + 1];
-      for (int64_t k = A.colptr[j] + lane; k < k1; k += 32) acc += (double)A.cval[k] * __ldcg(A.w + A.crow[k]);
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        const double pj = __ldcg(A.z + j) + beta * __ldcg(A.p + j);
-        __stcg(A.p + j, pj);
-        const double v = acc + (double)A.prow[j] * wstar;
-        const double qj = (A.crho[j] * pj - v) * A.inv_eta + A.shift * pj;
-        __stcg(A.q + j, qj);
-        lpq += pj * qj;
+    if (!grid_barrier(A.bar, nullptr, A.err, A.budget_ns)) return;
+    // ---- C: vector updates, w = A u, partial dots
+    const double tstar = A.a[A.istar] * (Qr - alpha * (Qw + beta * Qs));
+    double dg = 0.0, dd = 0.0, dr = 0.0, qr2 = 0.0, qw2 = 0.0, qs2 = 0.0;
+    const int64_t qc = (A.n + ngroups - 1) / ngroups;
+    for (int64_t q = 0; q < qc; ++q) {
+      const int64_t j = j0 + q * ngroups;
+      T acc = T(0);
+      if (j >= A.n) {
+        // no column for this group in this round
+      } else if (q == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (gl + e * G < c_len) acc += c_val[e] * __ldcg(A.t + c_row[e]);
+        for (int k = gl + E * G; k < c_len; k += G) acc += A.cval[c_start + k] * __ldcg(A.t + A.crow[c_start + k]);
+      } else {
+        const int64_t k0 = A.colptr[j], k1 = A.colptr[j + 1];
+        for (int64_t k = k0 + gl; k < k1; k += G) acc += A.cval[k] * __ldcg(A.t + A.crow[k]);
       }
-    }
-    lpq = block_total<kPcgThreads>(lpq, sh);
-    if (threadIdx.x == 0) __stcg(partPQ + blockIdx.x, lpq);
-    if (!grid_barrier(bcount, bgen, A.err, A.deadline_ns)) return;
-    // ---- C: update
-    const double pq = reduce_parts(partPQ, nb);
-    const double alpha = pq > 0.0 ? rz_old / pq : 0.0;
-    lrz = 0.0;
-    lrr = 0.0;
-    for (int64_t j = gtid; j < A.n; j += nthr) {
-      const double pj = __ldcg(A.p + j);
-      __stcg(A.x + j, __ldcg(A.x + j) + alpha * pj);
-      const double rj = __ldcg(A.r + j) - alpha * __ldcg(A.q + j);
-      __stcg(A.r + j, rj);
-      const double zj = rj / A.diag[j];
-      __stcg(A.z + j, zj);
-      lrz += rj * zj;
-      lrr += rj * rj;
-    }
-    {
-      double t[2] = {lrz, lrr};
-      block_sum<kPcgThreads, 2>(t, sh);
-      if (threadIdx.x == 0) {
-        __stcg(partRZ + blockIdx.x, t[0]);
-        __stcg(partRR + blockIdx.x, t[1]);
+      acc = group_sum_t<G>(acc);
+      if (gl == 0 && j < A.n) {
+        const double2 rw = __ldcg(A.cs + 2 * j);
+        const double2 sd = __ldcg(A.cs + 2 * j + 1);
+        const double qj = (double)A.prow[j];
+        const double s_new = rw.y + beta * sd.x;
+        const double p_new = rw.x * sd.y + beta * __ldcg(A.p + j);
+        const double r_new = rw.x - alpha * s_new;
+        const double u_new = r_new * sd.y;
+        const double v = (double)acc + qj * tstar;
+        const double w_new = (A.crho[j] * u_new - v) * A.inv_eta + A.shift * u_new;
+        __stcg(A.x + j, __ldcg(A.x + j) + alpha * p_new);
+        __stcg(A.p + j, p_new);
+        __stcg(A.cs + 2 * j, make_double2(r_new, w_new));
+        __stcg(A.cs + 2 * j + 1, make_double2(s_new, sd.y));
+        if constexpr (F32) __stcg(A.cs32 + j, make_float4((float)r_new, (float)w_new, (float)s_new, (float)sd.y));
+        dg += r_new * u_new;
+        dd += w_new * u_new;
+        dr += r_new * r_new;
+        const double qd = qj * sd.y;
+        qr2 += qd * r_new;
+        qw2 += qd * w_new;
+        qs2 += qd * s_new;
       }
     }
-    if (!grid_barrier(bcount, bgen, A.err, A.deadline_ns)) return;
+    double t6[6] = {dg, dd, dr, qr2, qw2, qs2};
+    if (!grid_allreduce<kPcgThreads, 6>(t6, A.part, A.bar, A.err, A.budget_ns, sh)) return;
+    const double g1 = t6[0];
+    const double d1v = t6[1];
+    rr = t6[2];
+    Qr = t6[3];
+    Qw = t6[4];
+    Qs = t6[5];
+    if (warm) {
+      warm = false;
+      bnorm = sqrt(rr);
+      if (bnorm == 0.0 || !(d1v > 0.0)) break;
+      alpha = g1 / d1v;
+      beta = 0.0;
+      gam = g1;
+      continue;
+    }
     ++it;
-    if (pq <= 0.0) break;
+    if (sqrt(rr) <= A.rtol * bnorm || it >= A.maxit) break;
+    beta = g1 / gam;
+    const double den = d1v - beta * g1 / alpha;
+    if (!(den > 0.0)) break;
+    alpha = g1 / den;
+    gam = g1;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.scal[S_CG_ITERS] = (double)it;
+    A.scal[S_CG_RES] = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+  }
+}
+
+__global__ void k_len_stats(const int32_t* __restrict__ row_len, const int64_t* __restrict__ colptr, int m, int64_t n,
+                            double* scal) {
+  __shared__ int sh[64];
+  int mr = 0, mc = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) mr = max(mr, row_len[i]);
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mc = max(mc, (int)(colptr[j + 1] - colptr[j]));
+  for (int o = 16; o > 0; o >>= 1) {
+    mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = mr;
+    sh[32 + (threadIdx.x >> 5)] = mc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mr = max(mr, sh[w]);
+      mc = max(mc, sh[32 + w]);
+    }
+    scal[S_MAXROW] = mr;
+    scal[S_MAXCOL] = mc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Float32 CG for a float32 sparsified Hessian (mixed precision).  Same
+// Chronopoulos-Gear arrangement as k_pcg; the vectors, recurrences and
+// products are float32 (the operator itself is float32-accurate and the
+// solve stops at a relative residual >= 1e-6), the inner products are
+// accumulated in float-float and alpha, beta are formed in float64.
+// Column state per column: {r, w, s, 1/diag} (float4); x, p float.
+// ---------------------------------------------------------------------------
+struct Pcg32Args {
+  const int64_t* row_start;
+  const int32_t* row_len;
+  const int32_t* col;
+  const float* val;
+  const int64_t* colptr;
+  const int32_t* crow;
+  const float* cval;
+  const float* prow;
+  const float* a32;
+  const double* crho;
+  const double* diag;
+  const double* rhs;
+  double* x_out;
+  float* x;
+  float* p;
+  float4* cs;
+  float* t;
+  float* crho32;
+  float2* part;
+  unsigned int* bar;
+  int* err;
+  double* scal;
+  int m, istar;
+  int64_t n;
+  float inv_eta, shift;
+  double rtol;
+  int maxit;
+  unsigned long long budget_ns;
+};
+
+template <int G, int E>
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg32(Pcg32Args A) {
+  __shared__ float sh[2 * 6 * 32];
+  const int nb = gridDim.x;
+  const int gl = threadIdx.x & (G - 1);
+  const int gid = (int)(((int64_t)blockIdx.x * kPcgThreads + threadIdx.x) / G);
+  const int ngroups = nb * (kPcgThreads / G);
+  const int64_t gtid = (int64_t)blockIdx.x * kPcgThreads + threadIdx.x;
+  const int64_t nthr = (int64_t)nb * kPcgThreads;
+
+  const int i0 = gid;
+  int r_len = 0;
+  int64_t r_start = 0;
+  int r_col[E];
+  float r_val[E];
+  if (i0 < A.m && i0 != A.istar) {
+    r_start = A.row_start[i0];
+    r_len = A.row_len[i0];
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = gl + e * G;
+    r_col[e] = k < r_len ? A.col[r_start + k] : 0;
+    r_val[e] = k < r_len ? A.val[r_start + k] : 0.f;
+  }
+  const int64_t j0 = gid;
+  int64_t c_start = 0;
+  int c_len = 0;
+  int c_row[E];
+  float c_val[E];
+  if (j0 < A.n) {
+    c_start = A.colptr[j0];
+    c_len = (int)(A.colptr[j0 + 1] - c_start);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = gl + e * G;
+    c_row[e] = k < c_len ? A.crow[c_start + k] : 0;
+    c_val[e] = k < c_len ? A.cval[c_start + k] : 0.f;
+  }
+
+  // state r = rhs, w = s = p = x = 0; row i* (q) enters through q^T u, formed
+  // from three sums over the stored state as in k_pcg
+  float red[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t j = gtid; j < A.n; j += nthr) {
+    const float dinv = (float)(1.0 / A.diag[j]);
+    const float r0 = (float)A.rhs[j];
+    __stcg(A.cs + j, make_float4(r0, 0.f, 0.f, dinv));
+    __stcg(A.p + j, 0.f);
+    __stcg(A.x + j, 0.f);
+    __stcg(A.crho32 + j, (float)A.crho[j]);
+    red[3] += A.prow[j] * dinv * r0;
+  }
+  double tot[6];
+  if (!grid_allreduce_f<kPcgThreads, 6>(red, tot, A.part, A.bar, A.err, A.budget_ns, sh)) return;
+  double Qr = tot[3], Qw = 0.0, Qs = 0.0;
+
+  double alpha = 0.0, beta = 0.0, gam = 0.0, bnorm = 0.0, rr = 0.0;
+  bool warm = true;
+  int it = 0;
+  for (;;) {
+    const float a32 = (float)alpha, b32 = (float)beta;
+    // ---- R: t = a o (P u)
+    const int qr = (A.m + ngroups - 1) / ngroups;
+    for (int q = 0; q < qr; ++q) {
+      const int i = i0 + q * ngroups;
+      float acc = 0.f;
+      if (i < A.m && i != A.istar) {
+        if (q == 0) {
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            if (gl + e * G < r_len) acc += r_val[e] * u_from32(A.cs, r_col[e], a32, b32);
+          for (int k = gl + E * G; k < r_len; k += G) acc += A.val[r_start + k] * u_from32(A.cs, A.col[r_start + k], a32, b32);
+        } else {
+          const int64_t st = A.row_start[i];
+          const int ln = A.row_len[i];
+          for (int k = gl; k < ln; k += G) acc += A.val[st + k] * u_from32(A.cs, A.col[st + k], a32, b32);
+        }
+      }
+      acc = group_sum_t<G>(acc);
+      if (gl == 0 && i < A.m && i != A.istar) __stcg(A.t + i, A.a32[i] * acc);
+    }
+    if (!grid_barrier(A.bar, nullptr, A.err, A.budget_ns)) return;
+    // ---- C
+    const float tstar = A.a32[A.istar] * (float)(Qr - alpha * (Qw + beta * Qs));
+    float dsum[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int64_t qc = (A.n + ngroups - 1) / ngroups;
+    for (int64_t q = 0; q < qc; ++q) {
+      const int64_t j = j0 + q * ngroups;
+      float acc = 0.f;
+      if (j >= A.n) {
+      } else if (q == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (gl + e * G < c_len) acc += c_val[e] * __ldcg(A.t + c_row[e]);
+        for (int k = gl + E * G; k < c_len; k += G) acc += A.cval[c_start + k] * __ldcg(A.t + A.crow[c_start + k]);
+      } else {
+        const int64_t k0 = A.colptr[j], k1 = A.colptr[j + 1];
+        for (int64_t k = k0 + gl; k < k1; k += G) acc += A.cval[k] * __ldcg(A.t + A.crow[k]);
+      }
+      acc = group_sum_t<G>(acc);
+      if (gl == 0 && j < A.n) {
+        const float4 c = __ldcg(A.cs + j);
+        const float qj = A.prow[j];
+        const float s_new = c.y + b32 * c.z;
+        const float p_new = c.x * c.w + b32 * __ldcg(A.p + j);
+        const float r_new = c.x - a32 * s_new;
+        const float u_new = r_new * c.w;
+        const float v = acc + qj * tstar;
+        const float w_new = (__ldcg(A.crho32 + j) * u_new - v) * A.inv_eta + A.shift * u_new;
+        __stcg(A.x + j, __ldcg(A.x + j) + a32 * p_new);
+        __stcg(A.p + j, p_new);
+        __stcg(A.cs + j, make_float4(r_new, w_new, s_new, c.w));
+        const float qd = qj * c.w;
+        dsum[0] += r_new * u_new;
+        dsum[1] += w_new * u_new;
+        dsum[2] += r_new * r_new;
+        dsum[3] += qd * r_new;
+        dsum[4] += qd * w_new;
+        dsum[5] += qd * s_new;
+      }
+    }
+    if (!grid_allreduce_f<kPcgThreads, 6>(dsum, tot, A.part, A.bar, A.err, A.budget_ns, sh)) return;
+    const double g1 = tot[0];
+    const double d1v = tot[1];
+    rr = tot[2];
+    Qr = tot[3];
+    Qw = tot[4];
+    Qs = tot[5];
+    if (warm) {
+      warm = false;
+      bnorm = sqrt(rr);
+      if (bnorm == 0.0 || !(d1v > 0.0)) break;
+      alpha = g1 / d1v;
+      beta = 0.0;
+      gam = g1;
+      continue;
+    }
+    ++it;
+    if (sqrt(rr) <= A.rtol * bnorm || it >= A.maxit) break;
+    beta = g1 / gam;
+    const double den = d1v - beta * g1 / alpha;
+    if (!(den > 0.0)) break;
+    alpha = g1 / den;
+    gam = g1;
+  }
+  for (int64_t j = gtid; j < A.n; j += nthr) A.x_out[j] = (double)__ldcg(A.x + j);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     A.scal[S_CG_ITERS] = (double)it;
     A.scal[S_CG_RES] = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
@@ -309,7 +582,13 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg(PcgArgs<T> A) {
 
 }  // namespace
 
-int pcg_max_blocks(int nsm) { return nsm * 4; }
+int pcg_max_blocks(int nsm) { return nsm; }
+
+cudaError_t launch_len_stats(const SparseBufs& S, int m, int64_t n, double* scal, cudaStream_t st) {
+  k_len_stats<<<1, 1024, 0, st>>>(S.row_len, S.colptr, m, n, scal);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_csc_build(const SparseBufs& S, int m, int64_t n, int64_t ldk, int nb, int rpb, bool fp64,
                              const double* a, int istar, double eta, cudaStream_t st) {
@@ -355,20 +634,38 @@ cudaError_t launch_export_sparse(const SparseBufs& S, int m, int64_t n, int ista
   return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t launch_pcg_t(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, int istar,
-                                const double* a, double eta, double shift, double rtol, int maxit, double timeout_s,
-                                int nsm, double* scal, cudaStream_t st) {
+template <int G, int E>
+static cudaError_t launch_pcg32_g(Pcg32Args& A, int nsm, cudaStream_t st) {
   static int occ = 0;
   if (occ == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T>, kPcgThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32<G, E>, kPcgThreads, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
   }
-  // one block per SM keeps the barrier short; never more than fit co-resident
-  int nb = nsm;
-  if (nb > nsm * occ) nb = nsm * occ;
-  if (nb > pcg_max_blocks(nsm)) nb = pcg_max_blocks(nsm);
+  void* args[] = {(void*)&A};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void*)k_pcg32<G, E>, dim3(nsm), dim3(kPcgThreads), args, 0, st);
+}
+
+template <typename T, int G, int E>
+static cudaError_t launch_pcg_g(PcgArgs<T>& A, int nsm, cudaStream_t st) {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, G, E>, kPcgThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+  }
+  // one block per SM keeps the barriers short; all blocks are co-resident
+  const int nb = nsm;
+  void* args[] = {(void*)&A};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void*)k_pcg<T, G, E>, dim3(nb), dim3(kPcgThreads), args, 0, st);
+}
+
+template <typename T>
+static cudaError_t launch_pcg_t(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, int istar,
+                                const double* a, double eta, double shift, double rtol, int maxit, double timeout_s,
+                                int nsm, int64_t nnz, double* scal, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(B.err, 0, sizeof(int), st);
@@ -386,8 +683,12 @@ static cudaError_t launch_pcg_t(const SparseBufs& S, const PcgBufs& B, int m, in
   A.crho = S.crho;
   A.diag = S.diag;
   A.rhs = B.rhs;
-  A.x = B.x; A.r = B.r; A.z = B.z; A.p = B.p; A.q = B.q; A.w = B.w;
-  A.part = B.part;
+  A.x = B.x;
+  A.p = B.p;
+  A.cs = reinterpret_cast<double2*>(B.cs);
+  A.cs32 = reinterpret_cast<float4*>(B.cs32);
+  A.t = reinterpret_cast<T*>(B.t);
+  A.part = reinterpret_cast<float2*>(B.part);
   A.bar = B.bar;
   A.err = B.err;
   A.scal = scal;
@@ -398,18 +699,59 @@ static cudaError_t launch_pcg_t(const SparseBufs& S, const PcgBufs& B, int m, in
   A.shift = shift;
   A.rtol = rtol;
   A.maxit = maxit;
-  // bound on each barrier wait, in nanoseconds of the GPU global timer
-  A.deadline_ns = (unsigned long long)(timeout_s * 1e9);
-  void* args[] = {(void*)&A};
-  note_launch();
-  return cudaLaunchCooperativeKernel((const void*)k_pcg<T>, dim3(nb), dim3(kPcgThreads), args, 0, st);
+  A.budget_ns = (unsigned long long)(timeout_s * 1e9);  // bound on each barrier wait
+  // group width from the mean row length (rows and columns have the same mean)
+  const double avg = (double)nnz / (double)(m > 1 ? m : 1);
+  if (avg <= 12.0) return launch_pcg_g<T, 4, 4>(A, nsm, st);
+  if (avg <= 28.0) return launch_pcg_g<T, 8, 4>(A, nsm, st);
+  return launch_pcg_g<T, 32, 4>(A, nsm, st);
 }
 
 cudaError_t launch_pcg(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, int istar, bool fp64,
-                       const double* a, double eta, double shift, double rtol, int maxit, double timeout_s, int nsm,
-                       double* scal, cudaStream_t st) {
-  if (fp64) return launch_pcg_t<double>(S, B, m, n, istar, a, eta, shift, rtol, maxit, timeout_s, nsm, scal, st);
-  return launch_pcg_t<float>(S, B, m, n, istar, a, eta, shift, rtol, maxit, timeout_s, nsm, scal, st);
+                       const double* a, const float* a32, double eta, double shift, double rtol, int maxit,
+                       double timeout_s, int nsm, int64_t nnz, double* scal, cudaStream_t st) {
+  if (fp64)
+    return launch_pcg_t<double>(S, B, m, n, istar, a, eta, shift, rtol, maxit, timeout_s, nsm, nnz, scal, st);
+  cudaError_t e = cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(B.err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  Pcg32Args A;
+  A.row_start = S.row_start;
+  A.row_len = S.row_len;
+  A.col = S.pool_col;
+  A.val = (const float*)S.pool_val;
+  A.colptr = S.colptr;
+  A.crow = S.csc_row;
+  A.cval = (const float*)S.csc_val;
+  A.prow = (const float*)S.prow;
+  A.a32 = a32;
+  A.crho = S.crho;
+  A.diag = S.diag;
+  A.rhs = B.rhs;
+  A.x_out = B.x;
+  // float vectors carved from the float64 buffers (each has room for 2n floats)
+  A.x = reinterpret_cast<float*>(B.p);
+  A.p = reinterpret_cast<float*>(B.p) + n;
+  A.cs = reinterpret_cast<float4*>(B.cs32);
+  A.t = reinterpret_cast<float*>(B.t);
+  A.crho32 = reinterpret_cast<float*>(B.cs);
+  A.part = reinterpret_cast<float2*>(B.part);
+  A.bar = B.bar;
+  A.err = B.err;
+  A.scal = scal;
+  A.m = m;
+  A.istar = istar;
+  A.n = n;
+  A.inv_eta = (float)(1.0 / eta);
+  A.shift = (float)shift;
+  A.rtol = rtol;
+  A.maxit = maxit;
+  A.budget_ns = (unsigned long long)(timeout_s * 1e9);
+  const double avg = (double)nnz / (double)(m > 1 ? m : 1);
+  if (avg <= 12.0) return launch_pcg32_g<4, 4>(A, nsm, st);
+  if (avg <= 28.0) return launch_pcg32_g<8, 4>(A, nsm, st);
+  return launch_pcg32_g<32, 4>(A, nsm, st);
 }
 
 }  // namespace ibsn
