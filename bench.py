@@ -339,6 +339,9 @@ def main():
                                      "sinkhorn_iters", "polish_outer", "max_nnz", "dense_passes",
                                      "marg_viol", "converged")},
         "profile_ms": {k: round(v["ms"] / len(results), 2) for k, v in sorted(prof.items())},
+        "profile_calls": {k: v["calls"] // len(results) for k, v in sorted(prof.items())},
+        "profile_gbs": {k: round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) for k, v in sorted(prof.items())
+                        if v["ms"] > 0},
     }
     print(json.dumps(line), flush=True)
 

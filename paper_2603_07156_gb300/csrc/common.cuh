@@ -253,6 +253,37 @@ __device__ __forceinline__ void block_sum_f(float (&v)[K], float* sh) {
   }
 }
 
+// Minimum of a float64 value over a block without float64 arithmetic: doubles
+// are mapped to integers with the same order and reduced with integer ops.
+__device__ __forceinline__ long long dbl_order(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dbl_unorder(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+template <int NT>
+__device__ __forceinline__ double block_min_exact(double v, long long* sh) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long k = dbl_order(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long o2 = __shfl_xor_sync(0xffffffffu, k, o);
+    k = o2 < k ? o2 : k;
+  }
+  __syncthreads();
+  if (lane == 0) sh[w] = k;
+  __syncthreads();
+  long long t = lane < NW ? sh[lane] : 0x7fffffffffffffffLL;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long o2 = __shfl_xor_sync(0xffffffffu, t, o);
+    t = o2 < t ? o2 : t;
+  }
+  return dbl_unorder(t);
+}
+
 // Compensated (Kahan) accumulator for float; plain for double.
 template <typename T>
 struct Acc;

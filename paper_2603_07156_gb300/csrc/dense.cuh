@@ -58,6 +58,13 @@ struct DenseArgs {
   const double* v1d;
   const double* v2d;
   const double* v3d;
+  const float* gam32;      // certify: float copy of gamma
+  const float* v3lo;       // certify: v3d - v3 (float-float lo part)
+  const double* bounds;    // certify: [0] max |C|, [1] max |gamma| (device)
+  // float-float anchor build: w_j as hi + lo floats, lam as hi + lo floats
+  const float* wvh;
+  const float* wvl;
+  float lamh, laml;
 };
 
 template <typename T, int TG, int CH>
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
 
 // ---------------------------------------------------------------------------
 // Inexact stopping test (Eq. 8) with the rounding of Alg. 3.
-// v1 = omega_j = 1 - y_j, v2 = e_c,j (raw), s1 = S = ||e_c||_1.
+// v1 = omega_j = 1 - y_j, v2 = e_c,j (raw), v3 = log e_c,j, s1 = S = ||e_c||_1.
 // e_r,i = a_i sum_j P_ij omega_j (z = 1 because X = diag(a) P has row sums a).
 // D_phi = sum_ij [Xhat log(Xhat/X) - Xhat + X]; each term X h(Xhat/X) >= 0
 // with h(r) = r log r - r + 1.  rowout = e_r (nullable).
@@ -348,18 +355,25 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
   T dpart = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);  // t.x keeps the exponents x_ij
     const T mx = row_shift<T, TG, CH>(t, sht);
     // row sum and sum_j e_ij omega_j in one reduction
-    T R[2] = {t.exp_shift(mx), T(0)};
+    T R[2] = {T(0), T(0)};
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
+      T om[V];
       if (c < A.ldk) {
-        T om[V];
         load_vec(A.v1 + c, om);
+      } else {
 #pragma unroll
-        for (int e = 0; e < V; ++e) R[1] += t.x[s][e] * om[e];
+        for (int e = 0; e < V; ++e) om[e] = T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const T ev = exp_t(t.x[s][e] - mx);
+        R[0] += ev;
+        R[1] += ev * om[e];
       }
     }
     row_sum<T, TG, 2>(R, shf);
@@ -369,19 +383,22 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
     if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = (double)er;
     const T logai_m = log(ai) - mx - log(R[0]);  // log X_ij = x_ij + this
     const T erS = er * invS;
+    const T lerS = log(erS);                     // log of the row factor of extra
+    const T aiS = ai * invS0;
     T D[1] = {T(0)};
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
       if (c < A.ldk) {
-        T om[V], ec[V];
+        T om[V], ec[V], lec[V];
         load_vec(A.v1 + c, om);
         load_vec(A.v2 + c, ec);
+        load_vec(A.v3 + c, lec);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
           if (c + e >= A.n) continue;
           // Xhat = X y + extra, X = a_i P_ij, extra = e_r,i e_c,j / S
-          const T X = ai * (t.x[s][e] * invS0);
+          const T X = aiS * exp_t(t.x[s][e] - mx);
           const T extra = erS * ec[e];
           const T xh = X * (T(1) - om[e]) + extra;
           if (xh <= T(0)) {
@@ -389,12 +406,12 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
           } else if (extra <= X) {
             D[0] += X * h_of_1pu(extra / X - om[e]);     // |u| <= 1: no overflow
           } else {
-            // extra mass on a cell with tiny X: log X from the exponent
-            T kv[V], d[V];
-            load_vec(A.K + (int64_t)i * A.ldk + c, kv);
-            load_vec(A.dv + c, d);
-            const T logX = kv[e] + d[e] + logai_m;
-            D[0] += xh * (log(xh) - logX) - xh + X;
+            // extra mass on a cell with small X: log Xhat = log extra + log1p(X y / extra)
+            // with log extra = log(e_r,i / S) + log e_c,j, and log X from the exponent
+            const T ratio = X * (T(1) - om[e]) / extra;
+            const T l1 = ratio < T(1e-4) ? ratio : log1p(ratio);
+            const T logX = t.x[s][e] + logai_m;
+            D[0] += xh * (lerS + lec[e] + l1 - logX) - xh + X;
           }
         }
       }
@@ -694,11 +711,12 @@ __global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
 // ===========================================================================
 // Float-float passes.  The anchored matrix is held as two float planes,
 // K = Khi + Klo (Klo = fl32(K - Khi)).  A float32 evaluation of every entry
-// decides which entries do not underflow (exp(x - M) > 0 in float32); only
-// those are evaluated in float64 from Khi + Klo + d, and only their Klo is
-// read.  All nonzero contributions are therefore float64; the entries skipped
-// are below exp(-87) of the row maximum.
+// selects the entries above 2^-64 of the row maximum; only those are evaluated
+// in float64 from Khi + Klo + d, and only their Klo is read.  The others are
+// dropped: each is below 2^-64 of its row's largest entry, so the row sums and
+// the column sums sum_i a_i P_ij change by less than n 2^-64 < 1e-15 relative.
 // ===========================================================================
+constexpr float kFFKeep = 0x1p-64f;
 template <int TG, int CH>
 struct FFRow {
   static constexpr int V = 4;
@@ -708,6 +726,31 @@ struct FFRow {
     return ((double)__ldg(A.K + off) + (double)__ldg(A.Klo + off)) + A.dv64[c + e] - M;
   }
 };
+
+// C_ij as an unevaluated float pair hi + lo with |hi + lo - C_ij| <= 2^-46 C_ij
+// (exact for float costs; for grid costs C = scale q with the integer q exact in
+// float and scale split as sh + sl).
+__device__ __forceinline__ float2 cost_ff(const CostRef& c, int i, int64_t j, float sh, float sl) {
+  if (c.kind == 1) return make_float2(__ldg(static_cast<const float*>(c.C) + (int64_t)i * c.ldc + j), 0.f);
+  if (c.kind == 0) {
+    const double C = __ldg(static_cast<const double*>(c.C) + (int64_t)i * c.ldc + j);
+    const float h = (float)C;
+    return make_float2(h, (float)(C - (double)h));
+  }
+  const int ri = i / c.gw, ci = i - ri * c.gw;
+  const int rj = (int)j / c.gw, cj = (int)j - rj * c.gw;
+  const float q = (float)((ri - rj) * (ri - rj) + (ci - cj) * (ci - cj));
+  const float p = q * sh;
+  return make_float2(p, fmaf(q, sl, fmaf(q, sh, -p)));
+}
+
+// s += x (float-float, TwoSum)
+__device__ __forceinline__ void ff_acc(float& sh, float& sl, float x) {
+  const float t = sh + x;
+  const float bb = t - sh;
+  sl += (sh - (t - bb)) + (x - bb);
+  sh = t;
+}
 
 // plan pass: lse_i, c_j = sum_i a_i P_ij, sum_i a_i lse_i (Eqs. 6-7)
 template <int TG, int CH>
@@ -735,7 +778,7 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > 0.f) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+        if (t.x[s][e] > kFFKeep) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
     }
     double S[1] = {ps};
     block_sum_ff<TG, 1>(S, shf);
@@ -749,7 +792,7 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > 0.f) sm[c + e] += w * exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+        if (t.x[s][e] > kFFKeep) sm[c + e] += w * exp(FFRow<TG, CH>::x64(A, i, c, e, M));
     }
   }
   __syncthreads();
@@ -771,6 +814,8 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   double ppsi = 0.0, plog = 0.0;
+  // an entry can grow by exp(t max|Delta|/eta) at the trial point: keep more
+  const float keep = kFFKeep * (float)A.s2;
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
@@ -783,7 +828,7 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > 0.f) {
+        if (t.x[s][e] > keep) {
           const double ev = exp(FFRow<TG, CH>::x64(A, i, c, e, M));
           s0 += ev;
           s1 += ev * A.v1d[c + e];
@@ -803,7 +848,7 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > 0.f) {
+        if (t.x[s][e] > keep) {
           const double ev = exp(FFRow<TG, CH>::x64(A, i, c, e, M));
           sm[c + e] += w * (ev + ev * A.v1d[c + e]);
         }
@@ -821,9 +866,12 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   extern __shared__ double dyn_sm[];
-  __shared__ double shd[6 * (TG / 32)];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
+  __shared__ long long shl[TG / 32];
+  // |fl32(C) - fl32(gamma) - (C - gamma)| <= 2^-22 (max|C| + max|gamma|)
+  const float zbound = 2.f * (float)ldexp(A.bounds[0] + A.bounds[1], -22);
+  const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
   constexpr int V = 4;
   double* sm = dyn_sm;
   for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
@@ -838,24 +886,44 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
     const double M = (double)mx;
     t.exp_shift(mx);
     const double ai = A.a[i];
-    // sweep 1: row sum; dense float64 work: zeta_i, sum C^2, sum_j C_ij e_c,j / S
-    double s0 = 0.0, zmin = kInf, c2 = 0.0, cec = 0.0;
+    // sweep 1: row sum (float64, kept entries); zeta_i = min_j C_ij - gamma_j by a
+    // float32 scan whose candidates (within the float32 error bound of the
+    // minimum) are re-evaluated exactly; sum_j C_ij e_c,j / S in float-float
+    // (all terms >= 0); sum C^2 in float32 (it only scales Delta_kkt)
+    double s0 = 0.0;
+    float z32 = __builtin_huge_valf(), c2f = 0.f, ceh = 0.f, cel = 0.f;
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         if (c + e >= A.n) continue;
-        if (t.x[s][e] > 0.f) s0 += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
-        const double C = cost_at(A.cost, i, c + e);
-        zmin = fmin(zmin, C - A.gam[c + e]);
-        c2 += C * C;
-        cec += C * A.v3d[c + e];
+        if (t.x[s][e] > kFFKeep) s0 += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+        const float2 C = cost_ff(A.cost, i, c + e, csh, csl);
+        z32 = fminf(z32, C.x - A.gam32[c + e]);
+        c2f = fmaf(C.x, C.x, c2f);
+        // C e_c / S in float-float: exact product of the hi parts plus the cross terms
+        const float vh = A.v3[c + e];
+        const float p = C.x * vh;
+        cel += fmaf(C.x, A.v3lo[c + e], fmaf(C.y, vh, fmaf(C.x, vh, -p)));
+        ff_acc(ceh, cel, p);
       }
     }
-    double R[3] = {s0, c2, cec};
+    double R[3] = {s0, (double)c2f, (double)ceh + (double)cel};
     block_sum_ff<TG, 3>(R, shf);
-    const double zeta = -block_max<TG>(-zmin, shd);
+    const float m32 = -block_max<TG>(-z32, sht);
+    double zc = kInf;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        if (c + e >= A.n) continue;
+        if (cost_ff(A.cost, i, c + e, csh, csl).x - A.gam32[c + e] <= m32 + zbound)
+          zc = fmin(zc, cost_at(A.cost, i, c + e) - A.gam[c + e]);
+      }
+    }
+    const double zeta = block_min_exact<TG>(zc, shl);
     const double invS0 = 1.0 / R[0];
     // sweep 2: e_r, the plan part of the primal, complementarity, column sums
     double pom = 0.0, psum = 0.0, pr = 0.0, cu = 0.0;
@@ -864,7 +932,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e) {
-        if (c + e >= A.n || !(t.x[s][e] > 0.f)) continue;
+        if (c + e >= A.n || !(t.x[s][e] > kFFKeep)) continue;
         const double P = exp(FFRow<TG, CH>::x64(A, i, c, e, M)) * invS0;
         const double C = cost_at(A.cost, i, c + e);
         const double F = ai * P * A.v1d[c + e];
@@ -897,7 +965,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
 #pragma unroll
         for (int e = 0; e < V; ++e) {
           if (c + e >= A.n) continue;
-          const double P = t.x[s][e] > 0.f ? exp(FFRow<TG, CH>::x64(A, i, c, e, M)) * invS0 : 0.0;
+          const double P = t.x[s][e] > kFFKeep ? exp(FFRow<TG, CH>::x64(A, i, c, e, M)) * invS0 : 0.0;
           A.plan_out[(int64_t)i * A.n + c + e] = ai * P * A.v1d[c + e] + er * A.v3d[c + e];
         }
       }
@@ -930,7 +998,7 @@ __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > 0.f) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+        if (t.x[s][e] > kFFKeep) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
     }
     double S[1] = {ps};
     block_sum_ff<TG, 1>(S, shf);
@@ -941,7 +1009,7 @@ __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
       for (int e = 0; e < V; ++e)
         if (c + e < A.n)
           A.plan_out[(int64_t)i * A.n + c + e] =
-              t.x[s][e] > 0.f ? exp(FFRow<TG, CH>::x64(A, i, c, e, M)) / S[0] : 0.0;
+              t.x[s][e] > kFFKeep ? exp(FFRow<TG, CH>::x64(A, i, c, e, M)) / S[0] : 0.0;
     }
   }
 }

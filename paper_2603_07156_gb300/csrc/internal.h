@@ -75,6 +75,7 @@ enum Slot : int {
   S_CG_ITERS = 26, S_CG_RES = 27,
   S_NNZ = 28,
   S_MAXROW = 29, S_MAXCOL = 30,  // longest row / column of P_rho (diagnostics)
+  S_CMAX = 31, S_GMAX = 32,      // max C_ij, max_j |gamma_j| (adjacent: certificate bounds)
   S_NSLOTS = 64
 };
 
@@ -101,8 +102,9 @@ cudaError_t launch_armijo_accept(int64_t n, double eta, double t, const double* 
                                  const double* b, double* g, double* scal, cudaStream_t st);
 // per-column rounding inputs, written in float and float64: y, omega, e_c, e_c / S
 struct RoundVecs {
-  float *y32, *om32, *ec32, *ecs32;
-  double *y64, *om64, *ec64, *ecs64;
+  float *y32, *om32, *ec32, *ecs32, *lec32;
+  float* ecsl32;  // e_c / S - fl32(e_c / S): the float-float lo part
+  double *y64, *om64, *ec64, *ecs64, *lec64;  // lec = log e_c (-inf where e_c = 0)
 };
 cudaError_t launch_round_prep(int64_t n, const double* b, const double* c, const double* g, const RoundVecs& R,
                               double* scal, cudaStream_t st);
@@ -112,6 +114,8 @@ cudaError_t launch_validate_marginals(int64_t m, int64_t n, const double* a, con
                                       cudaStream_t st);
 cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal,
                                  cudaStream_t st);
+cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, cudaStream_t st);
+cudaError_t launch_set_slot(double* scal, int slot, double v, cudaStream_t st);
 cudaError_t launch_fill_pad(void* v, int64_t n, int64_t ldk, bool fp64, double value, cudaStream_t st);
 cudaError_t launch_neg(int64_t n, const double* x, double* y, cudaStream_t st);
 

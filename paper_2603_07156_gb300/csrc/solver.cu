@@ -148,7 +148,7 @@ struct ibsn_ctx {
   double* K64 = nullptr;    // float64 anchored matrix (plain float64 mode)
   double *Gam, *gam, *ganc, *dd, *c, *c2, *g, *delta, *logb, *wv, *colF;
   double *lse, *lse2, *er, *zeta;
-  float *d32, *em32, *a32;
+  float *d32, *em32, *a32, *gam32;
   double *d64, *em64;
   RoundVecs rv{};
   double *colpart, *rowpart, *blockbuf;
@@ -224,9 +224,10 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   double** mvec[] = {&X->lse, &X->lse2, &X->er, &X->zeta};
   for (double** v : mvec) *v = cv.take<double>(m);
   X->a32 = cv.take<float>(m);
-  float** fvec[] = {&X->d32, &X->em32, &X->rv.y32, &X->rv.om32, &X->rv.ec32, &X->rv.ecs32};
+  float** fvec[] = {&X->d32,      &X->em32,      &X->gam32,      &X->rv.y32,   &X->rv.om32,
+                    &X->rv.ec32, &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32};
   for (float** v : fvec) *v = cv.take<float>(ldk);
-  double** dvec[] = {&X->d64, &X->em64, &X->rv.y64, &X->rv.om64, &X->rv.ec64, &X->rv.ecs64};
+  double** dvec[] = {&X->d64, &X->em64, &X->rv.y64, &X->rv.om64, &X->rv.ec64, &X->rv.ecs64, &X->rv.lec64};
   for (double** v : dvec) *v = cv.take<double>(ldk);
   X->colpart = cv.take<double>((size_t)nbcap * ldk);
   X->rowpart = cv.take<double>((size_t)nbcap * kRowParts);
@@ -315,7 +316,7 @@ Mode mode_for(const ibsn_ctx* X, Pass p) {
 struct PassIn {
   const float *v1f = nullptr, *v2f = nullptr, *v3f = nullptr;
   const double *v1d = nullptr, *v2d = nullptr, *v3d = nullptr;
-  double s1 = 0.0;
+  double s1 = 0.0, s2 = 0.0;
   double *rowout = nullptr, *rowout2 = nullptr, *plan_out = nullptr;
   const double* gam = nullptr;
   bool sparsify = false, reanchor = false;
@@ -359,6 +360,10 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
   A.rowpart = X->rowpart;
   A.cost = X->cost;
   A.s1 = in.s1;
+  A.s2 = in.s2;
+  A.gam32 = X->gam32;
+  A.v3lo = X->rv.ecsl32;
+  A.bounds = X->scal + S_CMAX;
   A.rowout = in.rowout;
   A.rowout2 = in.rowout2;
   A.plan_out = in.plan_out;
@@ -546,6 +551,10 @@ int do_armijo_trial(ibsn_ctx* X, double t, double* dL, double* slope) {
   in.v1f = X->em32;
   in.v1d = X->em64;
   in.rowout = X->lse2;
+  // entry j moves by t Delta_j / eta at the trial point, so its ratio to the
+  // row maximum can grow by exp(2 t max|Delta| / eta): the float-float filter
+  // keeps entries above 2^-64 exp(-2 t max|Delta| / eta) of the anchor maximum
+  in.s2 = std::exp(-2.0 * t * X->h_scal[S_DELTAMAX]);
   RT(run_pass(X, Pass::Armijo, in, &g));
   RT(finish(X, g, X->c2, false, 2));
   RT(read_scal(X));
@@ -576,6 +585,8 @@ int do_stop(ibsn_ctx* X, double* dphi) {
   in.v1d = X->rv.om64;
   in.v2f = X->rv.ec32;
   in.v2d = X->rv.ec64;
+  in.v3f = X->rv.lec32;
+  in.v3d = X->rv.lec64;
   in.s1 = X->h_scal[S_ECSUM];
   in.rowout = X->er;
   RT(run_pass(X, Pass::Stop, in, &g));
@@ -606,6 +617,7 @@ int do_certify(ibsn_ctx* X, Cert* out, double* plan, double* zeta) {
   in.rowout = zeta ? zeta : X->zeta;
   in.rowout2 = X->er;
   in.plan_out = plan;
+  if (mode_for(X, Pass::Certify) == Mode::FF) CK(launch_certify_prep(X->n, X->gam, X->gam32, X->scal, X->st));
   RT(run_pass(X, Pass::Certify, in, &g));
   RT(finish(X, g, X->colF, false, 7));
   RT(read_scal(X));
@@ -688,8 +700,13 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   if (pr->cost_kind != IBSN_COST_GRID2D &&
       launch_validate_cost(pr->m, pr->n, pr->C, pr->ldc, pr->cost_kind, X->scal, st) != cudaSuccess)
     return fail(IBSN_ERR_CUDA);
-  if (pr->cost_kind == IBSN_COST_GRID2D && cudaMemsetAsync(&X->scal[S_CBAD], 0, sizeof(double), st) != cudaSuccess)
-    return fail(IBSN_ERR_CUDA);
+  if (pr->cost_kind == IBSN_COST_GRID2D) {
+    // max C of the grid cost: the two opposite corners
+    const double dh = (double)(pr->grid_h - 1), dw = (double)(pr->grid_w - 1);
+    if (cudaMemsetAsync(&X->scal[S_CBAD], 0, sizeof(double), st) != cudaSuccess ||
+        launch_set_slot(X->scal, S_CMAX, pr->cost_scale * (dh * dh + dw * dw), st) != cudaSuccess)
+      return fail(IBSN_ERR_CUDA);
+  }
   if (read_scal(X) != IBSN_OK) return fail(IBSN_ERR_CUDA);
   const double* h = X->h_scal;
   if (h[S_ABAD] > 0 || h[S_CBAD] > 0) return fail(IBSN_ERR_NONFINITE);
@@ -716,9 +733,10 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   cudaMemsetAsync(X->Gam, 0, sizeof(double) * X->n, st);
   cudaMemsetAsync(X->gam, 0, sizeof(double) * X->n, st);
   cudaMemsetAsync(X->ctr, 0, sizeof(unsigned int) * C_NCOUNTERS, st);
-  float* tf[] = {X->d32, X->em32, X->rv.y32, X->rv.om32, X->rv.ec32, X->rv.ecs32};
+  float* tf[] = {X->d32,      X->em32,      X->gam32,      X->rv.y32,   X->rv.om32,
+                 X->rv.ec32, X->rv.ecs32, X->rv.ecsl32, X->rv.lec32};
   for (float* v : tf) cudaMemsetAsync(v, 0, sizeof(float) * X->ldk, st);
-  double* td[] = {X->d64, X->em64, X->rv.y64, X->rv.om64, X->rv.ec64, X->rv.ecs64};
+  double* td[] = {X->d64, X->em64, X->rv.y64, X->rv.om64, X->rv.ec64, X->rv.ecs64, X->rv.lec64};
   for (double* v : td) cudaMemsetAsync(v, 0, sizeof(double) * X->ldk, st);
   if (cudaGetLastError() != cudaSuccess) return fail(IBSN_ERR_CUDA);
   *out = X;

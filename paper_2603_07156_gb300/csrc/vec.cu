@@ -211,6 +211,8 @@ __global__ void __launch_bounds__(kVB) k_round_prep(int64_t n, const double* b, 
     put2(R.om32, R.om64, j, om);
     put2(R.ec32, R.ec64, j, ec);
     put2(R.ecs32, R.ecs64, j, ec * invS);
+    R.ecsl32[j] = (float)(ec * invS - (double)(float)(ec * invS));
+    put2(R.lec32, R.lec64, j, log(ec));
   }
   if (threadIdx.x == 0) scal[S_ECSUM] = s;
 }
@@ -262,16 +264,34 @@ __global__ void __launch_bounds__(kVB) k_validate_marginals(int64_t m, int64_t n
 
 __global__ void k_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal) {
   unsigned int bad = 0;
+  double cmax = 0.0;
   const int64_t total = m * n;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / n, j = q - i * n;
     const double v = kind == 0 ? static_cast<const double*>(C)[i * ldc + j]
                                : (double)static_cast<const float*>(C)[i * ldc + j];
     if (!(v >= 0.0) || !isfinite(v)) ++bad;
+    else cmax = fmax(cmax, v);
   }
   bad = (unsigned)warp_sum((int)bad);
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&scal[S_CBAD], (double)bad);
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(&scal[S_CMAX]), (unsigned long long)__double_as_longlong(cmax));
 }
+
+// float copy of gamma and max_j |gamma_j| for the certificate's float32 c-transform scan
+__global__ void __launch_bounds__(kVB) k_certify_prep(int64_t n, const double* gam, float* gam32, double* scal) {
+  __shared__ double sh[kVB / 32];
+  double mx = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += kVB) {
+    gam32[j] = (float)gam[j];
+    mx = fmax(mx, fabs(gam[j]));
+  }
+  mx = bmax(mx, sh);
+  if (threadIdx.x == 0) scal[S_GMAX] = mx;
+}
+
+__global__ void k_set_slot(double* scal, int slot, double v) { scal[slot] = v; }
 
 __global__ void k_fill_pad(void* v, int64_t n, int64_t ldk, bool fp64, double value) {
   const int64_t j = n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -355,8 +375,20 @@ cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ld
                                  cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(&scal[S_CBAD], 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&scal[S_CMAX], 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
   if (kind != 0 && kind != 1) return cudaSuccess;
   k_validate_cost<<<1216, 256, 0, st>>>(m, n, C, ldc, kind, scal);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, cudaStream_t st) {
+  k_certify_prep<<<1, kVB, 0, st>>>(n, gam, gam32, scal);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_set_slot(double* scal, int slot, double v, cudaStream_t st) {
+  k_set_slot<<<1, 1, 0, st>>>(scal, slot, v);
   note_launch();
   return cudaGetLastError();
 }
