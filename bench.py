@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample")
     ap.add_argument("--max-cg", type=int, default=0, help="CG iteration cap per Newton direction (0: library default)")
+    ap.add_argument("--max-outer", type=int, default=0,
+                    help="outer iteration cap (0: library default); a small cap gives a short profiling case")
+    ap.add_argument("--nnz-cap", type=int, default=0,
+                    help="nonzeros reserved for the sparsified Hessian (0: library default)")
     return ap.parse_args()
 
 
@@ -225,6 +229,10 @@ def main():
     b = torch.tensor(b_np, dtype=torch.float64, device=dev)
     prob = G.Problem(a=a, b=b, eta=args.eta, grid=(h, h), cost_scale=scale)
     extra = {"max_cg": args.max_cg} if args.max_cg > 0 else {}
+    if args.max_outer > 0:
+        extra["max_outer"] = args.max_outer
+    if args.nnz_cap > 0:
+        extra["nnz_cap"] = args.nnz_cap
     prm = G.params(precision=args.precision, profile=1, **extra)
     ws = G.alloc_workspace(prob, prm)
     stream = torch.cuda.current_stream(dev)

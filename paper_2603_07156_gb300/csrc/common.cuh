@@ -191,6 +191,12 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   const FF s = ff_two_sum(a.hi, b.hi);
   return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
+// x * y for a float-float x and a float y (TwoProduct of the hi parts)
+__device__ __forceinline__ FF ff_mul_f(FF x, float y) {
+  const float p = x.hi * y;
+  return ff_fast_two_sum(p, fmaf(x.hi, y, -p) + x.lo * y);
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ FF ff_from(double v) {
   const float hi = (float)v;
   return {hi, (float)(v - (double)hi)};

@@ -752,11 +752,81 @@ __device__ __forceinline__ void ff_acc(float& sh, float& sl, float x) {
   sh = t;
 }
 
+// Entries whose anchored exponent K exceeds -kFFLoBand can pass the filter of
+// the float-float passes before the next anchor build: the filter keeps x - max
+// above -44.4 (2^-64), the Armijo pass widens that by up to 2 * 30, and the
+// offsets d_j move within [-16, 16] (the anchor is rebuilt beyond that).
+constexpr float kFFLoBand = 144.f;
+
+// Anchor build (float planes): E_ij = w_j - lam C_ij in float-float (error
+// about 2^-46 |lam C_ij|, far below the float32 plane's rounding), row shift
+// M_i = max_j hi(E_ij), K32 = fl32(E - M).  In the polish (Klo_out set) the
+// lo plane Klo = fl32(K - K32) must carry float64 accuracy for every entry
+// the float-float passes can keep, so those entries (K > -kFFLoBand) are
+// re-evaluated in float64; the rest keep the float-float lo part.
+template <int TG, int CH>
+__global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
+  __shared__ float sht[TG / 32];
+  constexpr int V = 4;
+  const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
+  int r0, r1;
+  row_range(A.m, A.rows_per_block, r0, r1);
+  for (int i = r0; i < r1; ++i) {
+    float eh[CH][V], el[CH][V];
+    float mx = -__builtin_huge_valf();
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        if (c + e < A.n) {
+          const float2 C = cost_ff(A.cost, i, c + e, csh, csl);
+          const float p = A.lamh * C.x;  // lam C = p + pl (TwoProduct of the hi parts)
+          const float pl = fmaf(A.lamh, C.x, -p) + fmaf(A.lamh, C.y, A.laml * C.x);
+          const FF d = ff_add(FF{__ldg(A.wvh + c + e), __ldg(A.wvl + c + e)}, FF{-p, -pl});
+          eh[s][e] = d.hi;
+          el[s][e] = d.lo;
+          mx = fmaxf(mx, d.hi);
+        } else {
+          eh[s][e] = -__builtin_huge_valf();
+          el[s][e] = 0.f;
+        }
+      }
+    }
+    mx = block_max<TG>(mx, sht);
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = Tile<float, TG, CH>::col(s);
+      if (c < A.ldk) {
+        float kv[V], lo[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          if (c + e < A.n) {
+            const FF k = ff_add(FF{eh[s][e], el[s][e]}, FF{-mx, 0.f});
+            kv[e] = k.hi;
+            lo[e] = k.lo;
+            if (A.Klo_out != nullptr && k.hi > -kFFLoBand) {
+              const double K64 = (A.wv[c + e] - A.lam * cost_at(A.cost, i, c + e)) - (double)mx;
+              kv[e] = (float)K64;
+              lo[e] = (float)(K64 - (double)kv[e]);
+            }
+          } else {
+            kv[e] = -__builtin_huge_valf();
+            lo[e] = 0.f;
+          }
+        }
+        store_vec(A.Kout + (int64_t)i * A.ldk + c, kv);
+        if (A.Klo_out != nullptr) store_vec(A.Klo_out + (int64_t)i * A.ldk + c, lo);
+      }
+    }
+  }
+}
+
 // plan pass: lse_i, c_j = sum_i a_i P_ij, sum_i a_i lse_i (Eqs. 6-7)
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
   extern __shared__ double dyn_sm[];
-  __shared__ double shd[2 * (TG / 32)];
+  __shared__ double s_w;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
@@ -782,11 +852,17 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
     }
     double S[1] = {ps};
     block_sum_ff<TG, 1>(S, shf);
-    const double lse = M + log(S[0]);
-    const double ai = A.a[i];
-    lpart += ai * lse;
-    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = lse;
-    const double w = ai / S[0];
+    // per-row float64 scalars in one thread (float64 throughput is low: the
+    // whole block computing them would cost more than the row's traffic)
+    if (threadIdx.x == 0) {
+      const double lse = M + log(S[0]);
+      const double ai = A.a[i];
+      lpart += ai * lse;
+      if (A.rowout != nullptr) A.rowout[i] = lse;
+      s_w = ai / S[0];
+    }
+    __syncthreads();
+    const double w = s_w;
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<float, TG, CH>::col(s);
@@ -804,7 +880,7 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
   extern __shared__ double dyn_sm[];
-  __shared__ double shd[2 * (TG / 32)];
+  __shared__ double s_w;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
@@ -836,13 +912,17 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
     }
     double S[2] = {s0, s1};
     block_sum_ff<TG, 2>(S, shf);
-    const double si = S[1] / S[0];
-    const double ai = A.a[i];
-    const double l1p = log1p(si);
-    ppsi += ai * psi_log1p_minus(si);
-    plog += ai * l1p;
-    if (A.rowout != nullptr && threadIdx.x == 0) A.rowout[i] = M + log(S[0]) + l1p;
-    const double w = ai / (S[0] * (1.0 + si));
+    if (threadIdx.x == 0) {  // per-row float64 scalars in one thread
+      const double si = S[1] / S[0];
+      const double ai = A.a[i];
+      const double l1p = log1p(si);
+      ppsi += ai * psi_log1p_minus(si);
+      plog += ai * l1p;
+      if (A.rowout != nullptr) A.rowout[i] = M + log(S[0]) + l1p;
+      s_w = ai / (S[0] * (1.0 + si));
+    }
+    __syncthreads();
+    const double w = s_w;
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<float, TG, CH>::col(s);
@@ -869,6 +949,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   __shared__ long long shl[TG / 32];
+  __shared__ double s_inv, s_er;
   // |fl32(C) - fl32(gamma) - (C - gamma)| <= 2^-22 (max|C| + max|gamma|)
   const float zbound = 2.f * (float)ldexp(A.bounds[0] + A.bounds[1], -22);
   const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
@@ -924,7 +1005,9 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
       }
     }
     const double zeta = block_min_exact<TG>(zc, shl);
-    const double invS0 = 1.0 / R[0];
+    if (threadIdx.x == 0) s_inv = 1.0 / R[0];
+    __syncthreads();
+    const double invS0 = s_inv;
     // sweep 2: e_r, the plan part of the primal, complementarity, column sums
     double pom = 0.0, psum = 0.0, pr = 0.0, cu = 0.0;
 #pragma unroll
@@ -945,20 +1028,23 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
     }
     double Q[4] = {pom, psum, pr, cu};
     block_sum_ff<TG, 4>(Q, shf);
-    const double er = ai * Q[0];
-    const double rv = ai * (Q[1] - 1.0);
-    part[0] += Q[2] + er * R[2];
-    part[1] += ai * zeta;
-    part[2] += fabs(rv);
-    part[3] += er;
-    part[4] += Q[3];
-    part[5] += R[1];
-    part[6] += rv * rv;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // per-row float64 scalars in one thread
+      const double er = ai * Q[0];
+      const double rv = ai * (Q[1] - 1.0);
+      part[0] += Q[2] + er * R[2];
+      part[1] += ai * zeta;
+      part[2] += fabs(rv);
+      part[3] += er;
+      part[4] += Q[3];
+      part[5] += R[1];
+      part[6] += rv * rv;
       if (A.rowout != nullptr) A.rowout[i] = zeta;
       if (A.rowout2 != nullptr) A.rowout2[i] = er;
+      s_er = er;
     }
     if (A.plan_out != nullptr) {
+      __syncthreads();
+      const double er = s_er;
 #pragma unroll
       for (int s = 0; s < CH; ++s) {
         const int64_t c = Tile<float, TG, CH>::col(s);

@@ -129,6 +129,7 @@ static const void* ff_kernel(Pass p) {
     case Pass::Armijo: return (const void*)k_armijo_ff<TG, CH>;
     case Pass::Certify: return (const void*)k_certify_ff<TG, CH>;
     case Pass::Export: return (const void*)k_export_ff<TG, CH>;
+    case Pass::Reanchor: return (const void*)k_reanchor_ff<TG, CH>;
     default: return nullptr;
   }
 }
@@ -152,7 +153,7 @@ inline cudaError_t launch_dense_ff_t(Pass p, DenseArgs<float>& A, int nsm, cudaS
   const void* fn = ff_kernel_for(q, p);
   if (fn == nullptr) return cudaErrorInvalidValue;
   const int tg = TileTable<float>::tg[q];
-  const size_t smem = (p == Pass::Export) ? 0 : (size_t)A.ldk * sizeof(double);
+  const size_t smem = (p == Pass::Export || p == Pass::Reanchor) ? 0 : (size_t)A.ldk * sizeof(double);
   static std::mutex mu;
   static int occ_cache[TileTable<float>::count][(int)Pass::kCount] = {};
   static size_t smem_set[TileTable<float>::count][(int)Pass::kCount] = {};

@@ -88,7 +88,8 @@ cudaError_t launch_finish_cols(const double* colpart, int nb, int64_t ldk, int64
 
 // single-block vector kernels; `dT` is float or double per `fp64`
 cudaError_t launch_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam, double* ganc,
-                              const double* logb, double* wv, double* dd, float* d32, double* d64, cudaStream_t st);
+                              const double* logb, double* wv, float* wvh, float* wvl, double* dd, float* d32,
+                              double* d64, cudaStream_t st);
 cudaError_t launch_sinkhorn_update(int64_t n, double eta, const double* b, const double* c, double* gam,
                                    const double* ganc, double* dd, float* d32, double* d64, bool fp64,
                                    double* scal, cudaStream_t st);

@@ -148,7 +148,7 @@ struct ibsn_ctx {
   double* K64 = nullptr;    // float64 anchored matrix (plain float64 mode)
   double *Gam, *gam, *ganc, *dd, *c, *c2, *g, *delta, *logb, *wv, *colF;
   double *lse, *lse2, *er, *zeta;
-  float *d32, *em32, *a32, *gam32;
+  float *d32, *em32, *a32, *gam32, *wvh, *wvl;
   double *d64, *em64;
   RoundVecs rv{};
   double *colpart, *rowpart, *blockbuf;
@@ -224,8 +224,8 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   double** mvec[] = {&X->lse, &X->lse2, &X->er, &X->zeta};
   for (double** v : mvec) *v = cv.take<double>(m);
   X->a32 = cv.take<float>(m);
-  float** fvec[] = {&X->d32,      &X->em32,      &X->gam32,      &X->rv.y32,   &X->rv.om32,
-                    &X->rv.ec32, &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32};
+  float** fvec[] = {&X->d32,      &X->em32,      &X->gam32,      &X->rv.y32,   &X->rv.om32, &X->rv.ec32,
+                    &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32, &X->wvh,      &X->wvl};
   for (float** v : fvec) *v = cv.take<float>(ldk);
   double** dvec[] = {&X->d64, &X->em64, &X->rv.y64, &X->rv.om64, &X->rv.ec64, &X->rv.ecs64, &X->rv.lec64};
   for (double** v : dvec) *v = cv.take<double>(ldk);
@@ -381,7 +381,11 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
   }
   if (in.reanchor) {
     A.wv = X->wv;
+    A.wvh = X->wvh;
+    A.wvl = X->wvl;
     A.lam = in.lam;
+    A.lamh = (float)in.lam;
+    A.laml = (float)(in.lam - (double)A.lamh);
     if constexpr (F) {
       A.Kout = X->K32;
       A.Klo_out = X->prec == 2 ? X->Klo : nullptr;
@@ -398,7 +402,7 @@ double pass_bytes(ibsn_ctx* X, Pass p, Mode md) {
   const double sc = X->cost.kind == 0 ? 8.0 : (X->cost.kind == 1 ? 4.0 : 0.0);
   const double sk = md == Mode::F64 ? 8.0 : 4.0;
   switch (p) {
-    case Pass::Reanchor: return mn * ((X->prec == 2 ? 8.0 : sk) + sc);
+    case Pass::Reanchor: return mn * ((X->prec == 2 ? 8.0 : (md == Mode::F64 ? 8.0 : 4.0)) + sc);
     case Pass::Certify: return mn * (sk + sc);
     default: return mn * sk;
   }
@@ -406,7 +410,8 @@ double pass_bytes(ibsn_ctx* X, Pass p, Mode md) {
 
 // Launch one dense pass in the mode the context's precision selects.
 int run_pass(ibsn_ctx* X, Pass p, const PassIn& in, PassGeom* g = nullptr) {
-  const Mode md = p == Pass::Reanchor ? (X->prec == 0 ? Mode::F64 : Mode::F32) : mode_for(X, p);
+  // the float anchor is built in float-float arithmetic (K32, and Klo in the polish)
+  const Mode md = p == Pass::Reanchor ? (X->prec == 0 ? Mode::F64 : Mode::FF) : mode_for(X, p);
   ProfScope ps(X, pass_kind(p), pass_bytes(X, p, md), md != Mode::F32);
   if (md == Mode::F64) {
     DenseArgs<double> A = make_args<double>(X, in);
@@ -431,8 +436,8 @@ int finish(ibsn_ctx* X, const PassGeom& g, double* c_out, bool grad, int nrp) {
 
 // a1: anchor build for the current (k, Gamma, gamma) in precision X->prec
 int do_reanchor(ibsn_ctx* X) {
-  CK(launch_set_anchor(X->n, X->ldk, X->eta, X->Gam, X->gam, X->ganc, X->logb, X->wv, X->dd, X->d32, X->d64,
-                       X->st));
+  CK(launch_set_anchor(X->n, X->ldk, X->eta, X->Gam, X->gam, X->ganc, X->logb, X->wv, X->wvh, X->wvl, X->dd,
+                       X->d32, X->d64, X->st));
   PassIn in;
   in.reanchor = true;
   in.lam = (double)(X->k + 1) / X->eta;

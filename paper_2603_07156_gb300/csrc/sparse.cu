@@ -396,6 +396,114 @@ __global__ void k_len_stats(const int32_t* __restrict__ row_len, const int64_t* 
 // accumulated in float-float and alpha, beta are formed in float64.
 // Column state per column: {r, w, s, 1/diag} (float4); x, p float.
 // ---------------------------------------------------------------------------
+// Grid all-reduce of the six float CG sums for k_pcg32 (float-float, fixed
+// order).  Every block publishes its six partials as one 64-byte record
+// (float2 x 6, padded to 8), arrives at the grid counter and waits (bounded as
+// in grid_barrier); then one thread per block partial loads that block's
+// record with three 16-byte loads, so all partials are in flight at once, and
+// the block's warps reduce them.  Only thread 0 receives the totals (tot, as
+// float-float pairs); the caller broadcasts what the other threads need.
+// Returns false to every thread when the wait ran out or *err was set.
+__device__ __forceinline__ bool pcg_allreduce6(const float (&vin)[6], FF (&tot)[6], float4* part,
+                                               unsigned int* count, int* err, unsigned long long budget_ns,
+                                               float* sh) {
+  constexpr int NW = kPcgThreads / 32;
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nb = (int)gridDim.x;
+  FF f[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) f[q] = warp_sum_ff(FF{vin[q], 0.f});
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      sh[2 * (q * NW + w)] = f[q].hi;
+      sh[2 * (q * NW + w) + 1] = f[q].lo;
+    }
+  }
+  __syncthreads();
+  if (w == 0) {
+    FF t[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      t[q] = lane < NW ? FF{sh[2 * (q * NW + lane)], sh[2 * (q * NW + lane) + 1]} : FF{0.f, 0.f};
+      t[q] = warp_sum_ff(t[q]);
+    }
+    if (lane == 0) {
+      float4* rec = part + (size_t)blockIdx.x * 4;
+      __stcg(rec + 0, make_float4(t[0].hi, t[0].lo, t[1].hi, t[1].lo));
+      __stcg(rec + 1, make_float4(t[2].hi, t[2].lo, t[3].hi, t[3].lo));
+      __stcg(rec + 2, make_float4(t[4].hi, t[4].lo, t[5].hi, t[5].lo));
+      int ok = 1;
+      unsigned int old;
+      asm volatile("fence.acq_rel.gpu;\n\tatom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+      const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
+      unsigned int spins = 0;
+      unsigned long long t0 = 0;
+      for (;;) {
+        unsigned int cur;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+        if ((int)(cur - target) >= 0) break;
+        if ((++spins & 63u) == 0) {
+          if (*(volatile int*)err != 0) { ok = 0; break; }
+          const unsigned long long now = globaltimer_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if (now - t0 > budget_ns) {
+            atomicExch(err, (int)kDevTimeout);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      s_ok = ok;
+    }
+  }
+  __syncthreads();
+  if (!s_ok) return false;
+  // partial records: thread b loads block b's (b < nb <= kPcgThreads); the
+  // warp sums go to shared memory (reusing sh: all earlier reads are done)
+  constexpr int kRec = 12;  // floats per record in use
+  float* shr = sh;
+  const int nwr = (nb + 31) >> 5;
+  if (w < nwr) {
+    FF r[6];
+    const int b = threadIdx.x;
+    if (b < nb) {
+      const float4* rec = part + (size_t)b * 4;
+      const float4 v0 = __ldcg(rec + 0), v1 = __ldcg(rec + 1), v2 = __ldcg(rec + 2);
+      r[0] = FF{v0.x, v0.y};
+      r[1] = FF{v0.z, v0.w};
+      r[2] = FF{v1.x, v1.y};
+      r[3] = FF{v1.z, v1.w};
+      r[4] = FF{v2.x, v2.y};
+      r[5] = FF{v2.z, v2.w};
+    } else {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) r[q] = FF{0.f, 0.f};
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) r[q] = warp_sum_ff(r[q]);
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        shr[w * kRec + 2 * q] = r[q].hi;
+        shr[w * kRec + 2 * q + 1] = r[q].lo;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      FF a{0.f, 0.f};
+      for (int u = 0; u < nwr; ++u) a = ff_add(a, FF{shr[u * kRec + 2 * q], shr[u * kRec + 2 * q + 1]});
+      tot[q] = a;
+    }
+  }
+  return true;
+}
+
 struct Pcg32Args {
   const int64_t* row_start;
   const int32_t* row_len;
@@ -415,7 +523,7 @@ struct Pcg32Args {
   float4* cs;
   float* t;
   float* crho32;
-  float2* part;
+  float4* part;
   unsigned int* bar;
   int* err;
   double* scal;
@@ -480,15 +588,30 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg32(Pcg32Args A) {
     __stcg(A.crho32 + j, (float)A.crho[j]);
     red[3] += A.prow[j] * dinv * r0;
   }
-  double tot[6];
-  if (!grid_allreduce_f<kPcgThreads, 6>(red, tot, A.part, A.bar, A.err, A.budget_ns, sh)) return;
-  double Qr = tot[3], Qw = 0.0, Qs = 0.0;
-
-  double alpha = 0.0, beta = 0.0, gam = 0.0, bnorm = 0.0, rr = 0.0;
+  // The CG scalars live in thread 0; the other threads receive alpha, beta
+  // and t* through shared memory after each reduction.  alpha and beta are
+  // float (the vectors are float, so their rounding is of the same order);
+  // the totals arrive as float-float sums and t* = a_i* q^T u, a difference
+  // that can cancel, is formed in float-float.  No float64 work on this
+  // serial path: it runs once per iteration between two grid-wide waits.
+  __shared__ float s_a32, s_b32, s_tstar;
+  __shared__ int s_done;
+  FF tot[6];
+  if (!pcg_allreduce6(red, tot, A.part, A.bar, A.err, A.budget_ns, sh)) return;
+  FF Qr = tot[3], Qw{0.f, 0.f}, Qs{0.f, 0.f};
+  float alpha = 0.f, beta = 0.f, gam = 0.f, rr0 = 0.f, rr = 0.f;
+  const float rtol2 = (float)(A.rtol * A.rtol);
+  const float astar = A.a32[A.istar];
   bool warm = true;
   int it = 0;
+  if (threadIdx.x == 0) {
+    s_a32 = 0.f;
+    s_b32 = 0.f;
+    s_tstar = astar * Qr.hi;
+  }
+  __syncthreads();
   for (;;) {
-    const float a32 = (float)alpha, b32 = (float)beta;
+    const float a32 = s_a32, b32 = s_b32, tstar = s_tstar;
     // ---- R: t = a o (P u)
     const int qr = (A.m + ngroups - 1) / ngroups;
     for (int q = 0; q < qr; ++q) {
@@ -511,7 +634,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg32(Pcg32Args A) {
     }
     if (!grid_barrier(A.bar, nullptr, A.err, A.budget_ns)) return;
     // ---- C
-    const float tstar = A.a32[A.istar] * (float)(Qr - alpha * (Qw + beta * Qs));
     float dsum[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int64_t qc = (A.n + ngroups - 1) / ngroups;
     for (int64_t q = 0; q < qc; ++q) {
@@ -549,34 +671,56 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg32(Pcg32Args A) {
         dsum[5] += qd * s_new;
       }
     }
-    if (!grid_allreduce_f<kPcgThreads, 6>(dsum, tot, A.part, A.bar, A.err, A.budget_ns, sh)) return;
-    const double g1 = tot[0];
-    const double d1v = tot[1];
-    rr = tot[2];
-    Qr = tot[3];
-    Qw = tot[4];
-    Qs = tot[5];
-    if (warm) {
-      warm = false;
-      bnorm = sqrt(rr);
-      if (bnorm == 0.0 || !(d1v > 0.0)) break;
-      alpha = g1 / d1v;
-      beta = 0.0;
-      gam = g1;
-      continue;
+    if (!pcg_allreduce6(dsum, tot, A.part, A.bar, A.err, A.budget_ns, sh)) return;
+    if (threadIdx.x == 0) {
+      // Chronopoulos-Gear update (one thread per block; every block forms the
+      // same values from the same totals)
+      const float g1 = tot[0].hi;
+      const float d1v = tot[1].hi;
+      rr = tot[2].hi;
+      Qr = tot[3];
+      Qw = tot[4];
+      Qs = tot[5];
+      int done = 0;
+      if (warm) {
+        warm = false;
+        rr0 = rr;
+        if (!(rr0 > 0.f) || !(d1v > 0.f)) {
+          done = 1;
+        } else {
+          alpha = g1 / d1v;
+          beta = 0.f;
+          gam = g1;
+        }
+      } else {
+        ++it;
+        if (rr <= rtol2 * rr0 || it >= A.maxit) {
+          done = 1;
+        } else {
+          beta = g1 / gam;
+          const float den = d1v - beta * (g1 / alpha);
+          if (!(den > 0.f)) {
+            done = 1;
+          } else {
+            alpha = g1 / den;
+            gam = g1;
+          }
+        }
+      }
+      s_done = done;
+      s_a32 = alpha;
+      s_b32 = beta;
+      // row i* enters through q^T u = Qr - alpha (Qw + beta Qs) of the next iteration
+      const FF qu = ff_add(Qr, ff_neg(ff_mul_f(ff_add(Qw, ff_mul_f(Qs, beta)), alpha)));
+      s_tstar = astar * qu.hi;
     }
-    ++it;
-    if (sqrt(rr) <= A.rtol * bnorm || it >= A.maxit) break;
-    beta = g1 / gam;
-    const double den = d1v - beta * g1 / alpha;
-    if (!(den > 0.0)) break;
-    alpha = g1 / den;
-    gam = g1;
+    __syncthreads();
+    if (s_done) break;
   }
   for (int64_t j = gtid; j < A.n; j += nthr) A.x_out[j] = (double)__ldcg(A.x + j);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     A.scal[S_CG_ITERS] = (double)it;
-    A.scal[S_CG_RES] = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    A.scal[S_CG_RES] = rr0 > 0.f ? sqrt((double)rr / (double)rr0) : 0.0;
   }
 }
 
@@ -642,6 +786,8 @@ static cudaError_t launch_pcg32_g(Pcg32Args& A, int nsm, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
   }
+  // pcg_allreduce6 gives one thread of a block to each block's partial record
+  if (nsm > kPcgThreads) return cudaErrorInvalidConfiguration;
   void* args[] = {(void*)&A};
   note_launch();
   return cudaLaunchCooperativeKernel((const void*)k_pcg32<G, E>, dim3(nsm), dim3(kPcgThreads), args, 0, st);
@@ -736,7 +882,7 @@ cudaError_t launch_pcg(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, 
   A.cs = reinterpret_cast<float4*>(B.cs32);
   A.t = reinterpret_cast<float*>(B.t);
   A.crho32 = reinterpret_cast<float*>(B.cs);
-  A.part = reinterpret_cast<float2*>(B.part);
+  A.part = reinterpret_cast<float4*>(B.part);
   A.bar = B.bar;
   A.err = B.err;
   A.scal = scal;

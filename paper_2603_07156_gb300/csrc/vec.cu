@@ -71,13 +71,17 @@ __global__ void k_finish_cols(const double* __restrict__ colpart, int nb, int64_
 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVB) k_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam,
-                                                   double* ganc, const double* logb, double* wv, double* dd,
-                                                   float* d32, double* d64) {
+                                                   double* ganc, const double* logb, double* wv, float* wvh,
+                                                   float* wvl, double* dd, float* d32, double* d64) {
   for (int64_t j = threadIdx.x; j < ldk; j += kVB) {
     if (j < n) {
       const double G = (Gam ? Gam[j] : 0.0);
       ganc[j] = gam[j];
-      wv[j] = logb[j] + (G + gam[j]) / eta;
+      const double w = logb[j] + (G + gam[j]) / eta;
+      wv[j] = w;
+      const float h = (float)w;
+      wvh[j] = h;
+      wvl[j] = (float)(w - (double)h);
       dd[j] = 0.0;
     }
     put2(d32, d64, j, 0.0);
@@ -317,8 +321,9 @@ cudaError_t launch_finish_cols(const double* colpart, int nb, int64_t ldk, int64
 }
 
 cudaError_t launch_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam, double* ganc,
-                              const double* logb, double* wv, double* dd, float* d32, double* d64, cudaStream_t st) {
-  k_set_anchor<<<1, kVB, 0, st>>>(n, ldk, eta, Gam, gam, ganc, logb, wv, dd, d32, d64);
+                              const double* logb, double* wv, float* wvh, float* wvl, double* dd, float* d32,
+                              double* d64, cudaStream_t st) {
+  k_set_anchor<<<1, kVB, 0, st>>>(n, ldk, eta, Gam, gam, ganc, logb, wv, wvh, wvl, dd, d32, d64);
   note_launch();
   return cudaGetLastError();
 }
