@@ -26,6 +26,7 @@ struct DenseArgs {
   const T* v1;         // per-column input 1 (variant specific)
   const T* v2;         // per-column input 2
   const T* v3;         // per-column input 3
+  const T* v4;         // per-column input 4
   const double* a;     // m
   const T* aT;         // m, a in the pass precision
   double* rowout;      // m, variant specific (lse, e_r, zeta)
@@ -328,10 +329,18 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
 
 // ---------------------------------------------------------------------------
 // Inexact stopping test (Eq. 8) with the rounding of Alg. 3.
-// v1 = omega_j = 1 - y_j, v2 = e_c,j (raw), v3 = log e_c,j, s1 = S = ||e_c||_1.
-// e_r,i = a_i sum_j P_ij omega_j (z = 1 because X = diag(a) P has row sums a).
-// D_phi = sum_ij [Xhat log(Xhat/X) - Xhat + X]; each term X h(Xhat/X) >= 0
-// with h(r) = r log r - r + 1.  rowout = e_r (nullable).
+// v1 = omega_j = 1 - y_j, v2 = e_c,j, v3 = log e_c,j, v4 = (1-omega) log(1-omega)
+// + omega, s1 = S = ||e_c||_1.  e_r,i = a_i sum_j P_ij omega_j (z = 1: X = diag(a) P
+// has row sums a).  D_phi = sum_ij T_ij, T = Xhat log(Xhat/X) - Xhat + X >= 0 with
+// Xhat = X (1 - omega_j) + e_r,i e_c,j / S.  A column has omega_j > 0 or e_c,j > 0,
+// never both, so per entry (X = e^LX, extra = e_r,i e_c,j / S, L = log(extra/X)):
+//   e_c,j = 0:          T = X v4_j
+//   e_r,i = 0:          T = 0
+//   X <= tau extra:     T = extra (L - 1) + X (L + 1)   (error <= X tau / 2)
+//   otherwise:          T = X h(extra / X), h(u) = (1+u) log1p(u) - u
+// The second case, which holds for almost every entry off the plan's support,
+// needs no transcendental: L comes from the exponent and the logs of the row
+// and column factors.  rowout = e_r (nullable).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T h_of_1pu(T u) {
@@ -344,11 +353,23 @@ __device__ __forceinline__ T h_of_1pu(T u) {
   return (T(1) + u) * log1p(u) - u;
 }
 
+template <typename T>
+struct StopTau;
+template <>
+struct StopTau<float> {
+  static constexpr float v = 0x1p-12f;
+};
+template <>
+struct StopTau<double> {
+  static constexpr double v = 0x1p-24;
+};
+
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
+  constexpr T tau = StopTau<T>::v;
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   const T invS = (T)(A.s1 > 0.0 ? 1.0 / A.s1 : 0.0);
@@ -390,28 +411,24 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<T, TG, CH>::col(s);
       if (c < A.ldk) {
-        T om[V], ec[V], lec[V];
-        load_vec(A.v1 + c, om);
+        T ec[V], lec[V], hom[V];
         load_vec(A.v2 + c, ec);
         load_vec(A.v3 + c, lec);
+        load_vec(A.v4 + c, hom);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
           if (c + e >= A.n) continue;
-          // Xhat = X y + extra, X = a_i P_ij, extra = e_r,i e_c,j / S
           const T X = aiS * exp_t(t.x[s][e] - mx);
           const T extra = erS * ec[e];
-          const T xh = X * (T(1) - om[e]) + extra;
-          if (xh <= T(0)) {
-            D[0] += X;                                   // 0 log 0 - 0 + X
-          } else if (extra <= X) {
-            D[0] += X * h_of_1pu(extra / X - om[e]);     // |u| <= 1: no overflow
+          if (ec[e] <= T(0)) {
+            D[0] += X * hom[e];
+          } else if (!(extra > T(0))) {
+            // e_r,i = 0: Xhat = X on this column, T = 0
+          } else if (X <= tau * extra) {
+            const T L = (lerS + lec[e]) - (t.x[s][e] + logai_m);
+            D[0] += extra * (L - T(1)) + X * (L + T(1));
           } else {
-            // extra mass on a cell with small X: log Xhat = log extra + log1p(X y / extra)
-            // with log extra = log(e_r,i / S) + log e_c,j, and log X from the exponent
-            const T ratio = X * (T(1) - om[e]) / extra;
-            const T l1 = ratio < T(1e-4) ? ratio : log1p(ratio);
-            const T logX = t.x[s][e] + logai_m;
-            D[0] += xh * (lerS + lec[e] + l1 - logX) - xh + X;
+            D[0] += X * h_of_1pu(extra / X);
           }
         }
       }

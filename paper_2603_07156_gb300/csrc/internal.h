@@ -76,15 +76,22 @@ enum Slot : int {
   S_NNZ = 28,
   S_MAXROW = 29, S_MAXCOL = 30,  // longest row / column of P_rho (diagnostics)
   S_CMAX = 31, S_GMAX = 32,      // max C_ij, max_j |gamma_j| (adjacent: certificate bounds)
+  S_TMP = 33,                    // scratch total between two kernels of one step
   S_NSLOTS = 64
 };
 
 // Counter slots (unsigned) for last-block reductions and barriers.
 enum Counter : int { C_FINISH = 0, C_BAR_COUNT = 1, C_BAR_GEN = 2, C_POOL_LO = 4, C_NCOUNTERS = 16 };
 
+// Scratch of the multi-block O(n) reductions: a counter (zero between kernels)
+// and room for K block results per block.
+struct RedBuf {
+  unsigned int* counter;
+  double* blockbuf;
+};
 cudaError_t launch_finish_cols(const double* colpart, int nb, int64_t ldk, int64_t n, const double* b,
                                double* c_out, double* g_out, const double* rowpart, int nrp, double* scal,
-                               unsigned int* counter, double* blockbuf, cudaStream_t st);
+                               const RedBuf& rb, cudaStream_t st);
 
 // single-block vector kernels; `dT` is float or double per `fp64`
 cudaError_t launch_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam, double* ganc,
@@ -92,30 +99,34 @@ cudaError_t launch_set_anchor(int64_t n, int64_t ldk, double eta, const double* 
                               double* d64, cudaStream_t st);
 cudaError_t launch_sinkhorn_update(int64_t n, double eta, const double* b, const double* c, double* gam,
                                    const double* ganc, double* dd, float* d32, double* d64, bool fp64,
-                                   double* scal, cudaStream_t st);
+                                   double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_center(int64_t n, double eta, double* gam, const double* ganc, double* dd, float* d32,
-                          double* d64, double* scal, cudaStream_t st);
-cudaError_t launch_dir_post(int64_t n, double eta, double* delta, const double* g, double* scal, cudaStream_t st);
+                          double* d64, double* scal, const RedBuf& rb, cudaStream_t st);
+cudaError_t launch_dir_post(int64_t n, double eta, double* delta, const double* g, double* scal, const RedBuf& rb,
+                            cudaStream_t st);
 cudaError_t launch_armijo_prep(int64_t n, int64_t ldk, double eta, double t, const double* delta, const double* c,
-                               float* em32, double* em64, double* scal, cudaStream_t st);
+                               float* em32, double* em64, double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_armijo_accept(int64_t n, double eta, double t, const double* delta, double* gam,
                                  const double* ganc, double* dd, float* d32, double* d64, const double* cnew,
-                                 const double* b, double* g, double* scal, cudaStream_t st);
+                                 const double* b, double* g, double* scal, const RedBuf& rb, cudaStream_t st);
 // per-column rounding inputs, written in float and float64: y, omega, e_c, e_c / S
 struct RoundVecs {
   float *y32, *om32, *ec32, *ecs32, *lec32;
   float* ecsl32;  // e_c / S - fl32(e_c / S): the float-float lo part
+  float* hom32;   // (1 - omega) log(1 - omega) + omega
+  double* hom64;
   double *y64, *om64, *ec64, *ecs64, *lec64;  // lec = log e_c (-inf where e_c = 0)
 };
 cudaError_t launch_round_prep(int64_t n, const double* b, const double* c, const double* g, const RoundVecs& R,
                               double* scal, cudaStream_t st);
-cudaError_t launch_certify_cols(int64_t n, const double* b, const double* colF, const double* g_unused,
-                                const double* c, const double* gam, double ersum, double* scal, cudaStream_t st);
+cudaError_t launch_certify_cols(int64_t n, const double* b, const double* colF, const double* c, const double* gam,
+                                double ersum, double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_validate_marginals(int64_t m, int64_t n, const double* a, const double* b, double* scal,
                                       cudaStream_t st);
 cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal,
                                  cudaStream_t st);
-cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, cudaStream_t st);
+cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, const RedBuf& rb,
+                                cudaStream_t st);
 cudaError_t launch_set_slot(double* scal, int slot, double v, cudaStream_t st);
 cudaError_t launch_fill_pad(void* v, int64_t n, int64_t ldk, bool fp64, double value, cudaStream_t st);
 cudaError_t launch_neg(int64_t n, const double* x, double* y, cudaStream_t st);

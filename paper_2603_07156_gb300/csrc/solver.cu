@@ -225,13 +225,14 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   for (double** v : mvec) *v = cv.take<double>(m);
   X->a32 = cv.take<float>(m);
   float** fvec[] = {&X->d32,      &X->em32,      &X->gam32,      &X->rv.y32,   &X->rv.om32, &X->rv.ec32,
-                    &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32, &X->wvh,      &X->wvl};
+                    &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32, &X->wvh,      &X->wvl, &X->rv.hom32};
   for (float** v : fvec) *v = cv.take<float>(ldk);
-  double** dvec[] = {&X->d64, &X->em64, &X->rv.y64, &X->rv.om64, &X->rv.ec64, &X->rv.ecs64, &X->rv.lec64};
+  double** dvec[] = {&X->d64,       &X->em64,       &X->rv.y64,     &X->rv.om64,
+                     &X->rv.ec64,   &X->rv.ecs64,   &X->rv.lec64,   &X->rv.hom64};
   for (double** v : dvec) *v = cv.take<double>(ldk);
   X->colpart = cv.take<double>((size_t)nbcap * ldk);
   X->rowpart = cv.take<double>((size_t)nbcap * kRowParts);
-  X->blockbuf = cv.take<double>((n + 255) / 256 + 1);
+  X->blockbuf = cv.take<double>(4 * ((n + 31) / 32) + 8);
   X->sp.pool_col = cv.take<int32_t>(cap);
   X->sp.pool_val = cv.take<double>(cap);
   X->sp.row_start = cv.take<int64_t>(m);
@@ -258,6 +259,8 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   X->err = cv.take<int>(4);
   X->pool_top = cv.take<unsigned long long>(2);
 }
+
+RedBuf rb(ibsn_ctx* X) { return RedBuf{X->ctr + C_FINISH, X->blockbuf}; }
 
 int read_scal(ibsn_ctx* X) {
   CK(cudaMemcpyAsync(X->h_scal, X->scal, sizeof(double) * S_NSLOTS, cudaMemcpyDeviceToHost, X->st));
@@ -314,8 +317,8 @@ Mode mode_for(const ibsn_ctx* X, Pass p) {
 
 // Inputs of one dense pass beyond the common ones.
 struct PassIn {
-  const float *v1f = nullptr, *v2f = nullptr, *v3f = nullptr;
-  const double *v1d = nullptr, *v2d = nullptr, *v3d = nullptr;
+  const float *v1f = nullptr, *v2f = nullptr, *v3f = nullptr, *v4f = nullptr;
+  const double *v1d = nullptr, *v2d = nullptr, *v3d = nullptr, *v4d = nullptr;
   double s1 = 0.0, s2 = 0.0;
   double *rowout = nullptr, *rowout2 = nullptr, *plan_out = nullptr;
   const double* gam = nullptr;
@@ -334,12 +337,14 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
     A.v1 = in.v1f;
     A.v2 = in.v2f;
     A.v3 = in.v3f;
+    A.v4 = in.v4f;
   } else {
     A.K = X->K64;
     A.dv = X->d64;
     A.v1 = in.v1d;
     A.v2 = in.v2d;
     A.v3 = in.v3d;
+    A.v4 = in.v4d;
   }
   if constexpr (F) {
     A.aT = X->a32;
@@ -428,7 +433,7 @@ int run_pass(ibsn_ctx* X, Pass p, const PassIn& in, PassGeom* g = nullptr) {
 // finish a pass that wrote column partials: c_out = sum of partials, g = c - b
 int finish(ibsn_ctx* X, const PassGeom& g, double* c_out, bool grad, int nrp) {
   CK(launch_finish_cols(X->colpart, g.nb, X->ldk, X->n, grad ? X->b : nullptr, c_out, grad ? X->g : nullptr,
-                        X->rowpart, nrp, X->scal, X->ctr + C_FINISH, X->blockbuf, X->st));
+                        X->rowpart, nrp, X->scal, rb(X), X->st));
   return IBSN_OK;
 }
 
@@ -465,7 +470,7 @@ int do_plan(ibsn_ctx* X) {
 }
 
 int do_center(ibsn_ctx* X) {
-  CK(launch_center(X->n, X->eta, X->gam, X->ganc, X->dd, X->d32, X->d64, X->scal, X->st));
+  CK(launch_center(X->n, X->eta, X->gam, X->ganc, X->dd, X->d32, X->d64, X->scal, rb(X), X->st));
   return IBSN_OK;
 }
 
@@ -475,7 +480,7 @@ int do_sinkhorn(ibsn_ctx* X, double tol, int max_iter, int* iters) {
   int it = 0;
   while (X->gn >= tol && it < max_iter) {
     CK(launch_sinkhorn_update(X->n, X->eta, X->b, X->c, X->gam, X->ganc, X->dd, X->d32, X->d64, X->prec == 0,
-                              X->scal, X->st));
+                              X->scal, rb(X), X->st));
     RT(read_scal(X));
     RT(maybe_reanchor(X, X->h_scal[S_DMAX]));
     RT(do_plan(X));
@@ -534,7 +539,7 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
   RT(read_scal(X));
   if (perr == kDevTimeout) return IBSN_ERR_TIMEOUT;
   CK(cudaMemcpyAsync(X->delta, X->pc.x, sizeof(double) * X->n, cudaMemcpyDeviceToDevice, X->st));
-  CK(launch_dir_post(X->n, X->eta, X->delta, X->g, X->scal, X->st));
+  CK(launch_dir_post(X->n, X->eta, X->delta, X->g, X->scal, rb(X), X->st));
   RT(read_scal(X));
   if (iters) *iters = (int)X->h_scal[S_CG_ITERS];
   if (resid) *resid = X->h_scal[S_CG_RES];
@@ -550,7 +555,7 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
 
 // a6: one Armijo trial; dL = t g^T Delta + eta sum_j c_j phi_j + eta sum_i a_i psi(s_i)
 int do_armijo_trial(ibsn_ctx* X, double t, double* dL, double* slope) {
-  CK(launch_armijo_prep(X->n, X->ldk, X->eta, t, X->delta, X->c, X->em32, X->em64, X->scal, X->st));
+  CK(launch_armijo_prep(X->n, X->ldk, X->eta, t, X->delta, X->c, X->em32, X->em64, X->scal, rb(X), X->st));
   PassGeom g;
   PassIn in;
   in.v1f = X->em32;
@@ -571,7 +576,7 @@ int do_armijo_trial(ibsn_ctx* X, double t, double* dL, double* slope) {
 
 int do_accept(ibsn_ctx* X, double t) {
   CK(launch_armijo_accept(X->n, X->eta, t, X->delta, X->gam, X->ganc, X->dd, X->d32, X->d64, X->c2, X->b, X->g,
-                          X->scal, X->st));
+                          X->scal, rb(X), X->st));
   std::swap(X->c, X->c2);
   std::swap(X->lse, X->lse2);
   RT(read_scal(X));
@@ -592,6 +597,8 @@ int do_stop(ibsn_ctx* X, double* dphi) {
   in.v2d = X->rv.ec64;
   in.v3f = X->rv.lec32;
   in.v3d = X->rv.lec64;
+  in.v4f = X->rv.hom32;
+  in.v4d = X->rv.hom64;
   in.s1 = X->h_scal[S_ECSUM];
   in.rowout = X->er;
   RT(run_pass(X, Pass::Stop, in, &g));
@@ -622,7 +629,7 @@ int do_certify(ibsn_ctx* X, Cert* out, double* plan, double* zeta) {
   in.rowout = zeta ? zeta : X->zeta;
   in.rowout2 = X->er;
   in.plan_out = plan;
-  if (mode_for(X, Pass::Certify) == Mode::FF) CK(launch_certify_prep(X->n, X->gam, X->gam32, X->scal, X->st));
+  if (mode_for(X, Pass::Certify) == Mode::FF) CK(launch_certify_prep(X->n, X->gam, X->gam32, X->scal, rb(X), X->st));
   RT(run_pass(X, Pass::Certify, in, &g));
   RT(finish(X, g, X->colF, false, 7));
   RT(read_scal(X));
@@ -633,7 +640,7 @@ int do_certify(ibsn_ctx* X, Cert* out, double* plan, double* zeta) {
   const double comp = X->h_scal[S_ROW0 + 4];
   const double c2sum = X->h_scal[S_ROW0 + 5];
   const double rv2 = X->h_scal[S_ROW0 + 6];
-  CK(launch_certify_cols(X->n, X->b, X->colF, nullptr, X->c, X->gam, ersum, X->scal, X->st));
+  CK(launch_certify_cols(X->n, X->b, X->colF, X->c, X->gam, ersum, X->scal, rb(X), X->st));
   RT(read_scal(X));
   const double dual = azeta + X->h_scal[S_BGAM];
   out->p = primal;
@@ -739,9 +746,9 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   cudaMemsetAsync(X->gam, 0, sizeof(double) * X->n, st);
   cudaMemsetAsync(X->ctr, 0, sizeof(unsigned int) * C_NCOUNTERS, st);
   float* tf[] = {X->d32,      X->em32,      X->gam32,      X->rv.y32,   X->rv.om32,
-                 X->rv.ec32, X->rv.ecs32, X->rv.ecsl32, X->rv.lec32};
+                 X->rv.ec32, X->rv.ecs32, X->rv.ecsl32, X->rv.lec32, X->rv.hom32};
   for (float* v : tf) cudaMemsetAsync(v, 0, sizeof(float) * X->ldk, st);
-  double* td[] = {X->d64, X->em64, X->rv.y64, X->rv.om64, X->rv.ec64, X->rv.ecs64, X->rv.lec64};
+  double* td[] = {X->d64, X->em64, X->rv.y64, X->rv.om64, X->rv.ec64, X->rv.ecs64, X->rv.lec64, X->rv.hom64};
   for (double* v : td) cudaMemsetAsync(v, 0, sizeof(double) * X->ldk, st);
   if (cudaGetLastError() != cudaSuccess) return fail(IBSN_ERR_CUDA);
   *out = X;

@@ -26,74 +26,128 @@ __device__ __forceinline__ double bsum(double v, double* sh) {
 __device__ __forceinline__ double bmax(double v, double* sh) { return block_max<kVB>(v, sh); }
 
 // ---------------------------------------------------------------------------
-__global__ void k_finish_cols(const double* __restrict__ colpart, int nb, int64_t ldk, int64_t n,
-                              const double* __restrict__ b, double* c_out, double* g_out,
-                              const double* __restrict__ rowpart, int nrp, double* scal, unsigned int* counter,
-                              double* blockbuf) {
-  __shared__ double sh[8];
+// Grid-wide reductions of the O(n) kernels.  Every block reduces its K values
+// (sum, or max for the values flagged in kMax), writes them to blockbuf and
+// counts itself in; the last block to arrive combines the block results in
+// block order, so the totals do not depend on scheduling.  The O(n) kernels
+// run on many blocks: float64 arithmetic on one SM alone is slow.
+// ---------------------------------------------------------------------------
+constexpr int kRB = 256;  // threads per block of the O(n) kernels
+
+template <int K>
+__device__ __forceinline__ bool reduce_last(double (&v)[K], unsigned kMax, const RedBuf& rb) {
+  __shared__ double sh[K][kRB / 32];
   __shared__ bool last;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double g2 = 0.0;
-  if (j < n) {
-    double c = 0.0;
-    for (int q = 0; q < nb; ++q) c += colpart[(int64_t)q * ldk + j];
-    if (c_out) c_out[j] = c;
-    if (b) {
-      const double g = c - b[j];
-      if (g_out) g_out[j] = g;
-      g2 = g * g;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double x = v[q];
+    const bool mx = (kMax >> q) & 1u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = mx ? fmax(x, y) : x + y;
     }
-  }
-  double t[1] = {g2};
-  block_sum<256, 1>(t, sh);
-  if (threadIdx.x == 0) {
-    blockbuf[blockIdx.x] = t[0];
-    __threadfence();
-    const unsigned int prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
+    if (lane == 0) sh[q][w] = x;
   }
   __syncthreads();
-  if (last) {
-    __threadfence();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (unsigned q = 0; q < gridDim.x; ++q) s += ((volatile double*)blockbuf)[q];
-      scal[S_GN2] = s;
-      *counter = 0u;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double x = sh[q][0];
+      const bool mx = (kMax >> q) & 1u;
+      for (int u = 1; u < kRB / 32; ++u) x = mx ? fmax(x, sh[q][u]) : x + sh[q][u];
+      rb.blockbuf[(size_t)q * gridDim.x + blockIdx.x] = x;
     }
-    if (threadIdx.x < nrp) {
+    __threadfence();
+    last = atomicAdd(rb.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  if (threadIdx.x != 0) return false;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const bool mx = (kMax >> q) & 1u;
+    double x = ((volatile double*)rb.blockbuf)[(size_t)q * gridDim.x];
+    for (unsigned b = 1; b < gridDim.x; ++b) {
+      const double y = ((volatile double*)rb.blockbuf)[(size_t)q * gridDim.x + b];
+      x = mx ? fmax(x, y) : x + y;
+    }
+    v[q] = x;
+  }
+  *rb.counter = 0u;  // ready for the next kernel on the stream
+  return true;
+}
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * kRB + threadIdx.x; }
+
+// Column sums of the per-block partials of a dense pass: c = sum_q colpart[q],
+// g = c - b, ||g||^2 and ||max(0, -g)||_1 (the rounding's S), and the totals of
+// the first nrp row partials.  A block handles 32 columns x 8 slices of the
+// partials; the slices are added in slice order.
+__global__ void __launch_bounds__(kRB) k_finish_cols(const double* __restrict__ colpart, int nb, int64_t ldk,
+                                                     int64_t n, const double* __restrict__ b, double* c_out,
+                                                     double* g_out, const double* __restrict__ rowpart, int nrp,
+                                                     double* scal, RedBuf rb) {
+  __shared__ double part[8][33];
+  const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+  double c = 0.0;
+  if (j < n)
+    for (int q = sl; q < nb; q += 8) c += colpart[(int64_t)q * ldk + j];
+  part[sl][lane] = c;
+  __syncthreads();
+  double v[2] = {0.0, 0.0};
+  if (sl == 0 && j < n) {
+    double t = part[0][lane];
+#pragma unroll
+    for (int u = 1; u < 8; ++u) t += part[u][lane];
+    if (c_out) c_out[j] = t;
+    if (b) {
+      const double g = t - b[j];
+      if (g_out) g_out[j] = g;
+      v[0] = g * g;
+      v[1] = fmax(0.0, -g);
+    }
+  }
+  if (reduce_last<2>(v, 0u, rb)) {
+    if (b) {  // the gradient's totals stay valid until the next gradient
+      scal[S_GN2] = v[0];
+      scal[S_ECSUM] = v[1];
+    }
+    for (int q = 0; q < nrp; ++q) {
       double s = 0.0;
-      for (int q = 0; q < nb; ++q) s += rowpart[q * kRowParts + threadIdx.x];
-      scal[S_ROW0 + threadIdx.x] = s;
+      for (int u = 0; u < nb; ++u) s += rowpart[u * kRowParts + q];
+      scal[S_ROW0 + q] = s;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kVB) k_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam,
-                                                   double* ganc, const double* logb, double* wv, float* wvh,
-                                                   float* wvl, double* dd, float* d32, double* d64) {
-  for (int64_t j = threadIdx.x; j < ldk; j += kVB) {
-    if (j < n) {
-      const double G = (Gam ? Gam[j] : 0.0);
-      ganc[j] = gam[j];
-      const double w = logb[j] + (G + gam[j]) / eta;
-      wv[j] = w;
-      const float h = (float)w;
-      wvh[j] = h;
-      wvl[j] = (float)(w - (double)h);
-      dd[j] = 0.0;
-    }
-    put2(d32, d64, j, 0.0);
+__global__ void __launch_bounds__(kRB) k_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam,
+                                                   double* gam, double* ganc, const double* logb, double* wv,
+                                                   float* wvh, float* wvl, double* dd, float* d32, double* d64) {
+  const int64_t j = gtid();
+  if (j < n) {
+    const double G = (Gam ? Gam[j] : 0.0);
+    ganc[j] = gam[j];
+    const double w = logb[j] + (G + gam[j]) / eta;
+    wv[j] = w;
+    const float h = (float)w;
+    wvh[j] = h;
+    wvl[j] = (float)(w - (double)h);
+    dd[j] = 0.0;
   }
+  if (j < ldk) put2(d32, d64, j, 0.0);
 }
 
-__global__ void __launch_bounds__(kVB) k_sinkhorn_update(int64_t n, double eta, const double* b, const double* c,
+__global__ void __launch_bounds__(kRB) k_sinkhorn_update(int64_t n, double eta, const double* b, const double* c,
                                                         double* gam, const double* ganc, double* dd, float* d32,
-                                                        double* d64, bool fp64, double* scal) {
-  __shared__ double sh[64];
-  double mx = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) {
+                                                        double* d64, bool fp64, double* scal, RedBuf rb) {
+  const int64_t j = gtid();
+  double v[1] = {0.0};
+  if (j < n) {
     // a column whose plan entries all underflowed has c_j = 0; the floor keeps
     // the step finite (it only bounds the first steps of such columns)
     const double gj = gam[j] + eta * (log(b[j]) - log(fmax(c[j], fp64 ? 1e-300 : 1e-45)));
@@ -101,51 +155,51 @@ __global__ void __launch_bounds__(kVB) k_sinkhorn_update(int64_t n, double eta, 
     const double d = (gj - ganc[j]) / eta;
     dd[j] = d;
     put2(d32, d64, j, d);
-    mx = fmax(mx, fabs(d));
+    v[0] = fabs(d);
   }
-  mx = bmax(mx, sh);
-  if (threadIdx.x == 0) scal[S_DMAX] = mx;
+  if (reduce_last<1>(v, 1u, rb)) scal[S_DMAX] = v[0];
 }
 
-__global__ void __launch_bounds__(kVB) k_center(int64_t n, double eta, double* gam, const double* ganc, double* dd,
-                                               float* d32, double* d64, double* scal) {
-  __shared__ double sh[64];
-  double s = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) s += gam[j];
-  const double mean = bsum(s, sh) / (double)n;
-  double mx = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) {
+// sum of x into scal[slot] (first phase of a centring)
+__global__ void __launch_bounds__(kRB) k_sum_into(int64_t n, const double* x, double* scal, int slot, RedBuf rb) {
+  const int64_t j = gtid();
+  double v[1] = {j < n ? x[j] : 0.0};
+  if (reduce_last<1>(v, 0u, rb)) scal[slot] = v[0];
+}
+
+__global__ void __launch_bounds__(kRB) k_center(int64_t n, double eta, double* gam, const double* ganc, double* dd,
+                                               float* d32, double* d64, double* scal, RedBuf rb) {
+  const double mean = scal[S_MEAN] / (double)n;
+  const int64_t j = gtid();
+  double v[1] = {0.0};
+  if (j < n) {
     const double gj = gam[j] - mean;
     gam[j] = gj;
     const double d = (gj - ganc[j]) / eta;
     dd[j] = d;
     put2(d32, d64, j, d);
-    mx = fmax(mx, fabs(d));
+    v[0] = fabs(d);
   }
-  mx = bmax(mx, sh);
-  if (threadIdx.x == 0) {
-    scal[S_DMAX] = mx;
+  if (reduce_last<1>(v, 1u, rb)) {
+    scal[S_DMAX] = v[0];
     scal[S_MEAN] = mean;
   }
 }
 
-__global__ void __launch_bounds__(kVB) k_dir_post(int64_t n, double eta, double* delta, const double* g, double* scal) {
-  __shared__ double sh[64];
-  double s = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) s += delta[j];
-  const double mean = bsum(s, sh) / (double)n;
-  double sl = 0.0, mx = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) {
+__global__ void __launch_bounds__(kRB) k_dir_post(int64_t n, double eta, double* delta, const double* g, double* scal,
+                                                 RedBuf rb) {
+  const double mean = scal[S_TMP] / (double)n;
+  const int64_t j = gtid();
+  double v[2] = {0.0, 0.0};
+  if (j < n) {
     const double dj = delta[j] - mean;
     delta[j] = dj;
-    sl += g[j] * dj;
-    mx = fmax(mx, fabs(dj));
+    v[0] = g[j] * dj;
+    v[1] = fabs(dj);
   }
-  sl = bsum(sl, sh);
-  mx = bmax(mx, sh);
-  if (threadIdx.x == 0) {
-    scal[S_SLOPE] = sl;
-    scal[S_DELTAMAX] = mx / eta;
+  if (reduce_last<2>(v, 2u, rb)) {
+    scal[S_SLOPE] = v[0];
+    scal[S_DELTAMAX] = v[1] / eta;
   }
 }
 
@@ -155,91 +209,82 @@ __device__ __forceinline__ double phi_expm1_minus(double x) {
   return expm1(x) - x;
 }
 
-__global__ void __launch_bounds__(kVB) k_armijo_prep(int64_t n, int64_t ldk, double eta, double t, const double* delta,
-                                                    const double* c, float* em32, double* em64, double* scal) {
-  __shared__ double sh[64];
-  double ps = 0.0;
-  for (int64_t j = threadIdx.x; j < ldk; j += kVB) {
-    if (j < n) {
-      const double x = t * delta[j] / eta;
-      put2(em32, em64, j, expm1(x));
-      ps += c[j] * phi_expm1_minus(x);
-    } else {
-      put2(em32, em64, j, 0.0);
-    }
+__global__ void __launch_bounds__(kRB) k_armijo_prep(int64_t n, int64_t ldk, double eta, double t, const double* delta,
+                                                    const double* c, float* em32, double* em64, double* scal,
+                                                    RedBuf rb) {
+  const int64_t j = gtid();
+  double v[1] = {0.0};
+  if (j < n) {
+    const double x = t * delta[j] / eta;
+    put2(em32, em64, j, expm1(x));
+    v[0] = c[j] * phi_expm1_minus(x);
+  } else if (j < ldk) {
+    put2(em32, em64, j, 0.0);
   }
-  ps = bsum(ps, sh);
-  if (threadIdx.x == 0) scal[S_PHI] = ps;
+  if (reduce_last<1>(v, 0u, rb)) scal[S_PHI] = v[0];
 }
 
-__global__ void __launch_bounds__(kVB) k_armijo_accept(int64_t n, double eta, double t, const double* delta,
+__global__ void __launch_bounds__(kRB) k_armijo_accept(int64_t n, double eta, double t, const double* delta,
                                                       double* gam, const double* ganc, double* dd, float* d32,
                                                       double* d64, const double* cnew, const double* b, double* g,
-                                                      double* scal) {
-  __shared__ double sh[64];
-  double mx = 0.0, g2 = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) {
+                                                      double* scal, RedBuf rb) {
+  const int64_t j = gtid();
+  double v[3] = {0.0, 0.0, 0.0};
+  if (j < n) {
     const double gj = gam[j] + t * delta[j];
     gam[j] = gj;
     const double d = (gj - ganc[j]) / eta;
     dd[j] = d;
     put2(d32, d64, j, d);
-    mx = fmax(mx, fabs(d));
     const double gr = cnew[j] - b[j];
     g[j] = gr;
-    g2 += gr * gr;
+    v[0] = fabs(d);
+    v[1] = gr * gr;
+    v[2] = fmax(0.0, -gr);
   }
-  mx = bmax(mx, sh);
-  g2 = bsum(g2, sh);
-  if (threadIdx.x == 0) {
-    scal[S_DMAX] = mx;
-    scal[S_GN2] = g2;
+  if (reduce_last<3>(v, 1u, rb)) {
+    scal[S_DMAX] = v[0];
+    scal[S_GN2] = v[1];
+    scal[S_ECSUM] = v[2];
   }
 }
 
 // Alg. 3 with z = 1: y_j = min(b_j/c_j, 1), omega_j = 1 - y_j = max(0, g_j/c_j),
-// e_c,j = b_j - y_j c_j = max(0, -g_j), S = ||e_c||_1.
-__global__ void __launch_bounds__(kVB) k_round_prep(int64_t n, const double* b, const double* c, const double* g,
-                                                   RoundVecs R, double* scal) {
-  __shared__ double sh[64];
-  double s = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) s += fmax(0.0, -g[j]);
-  s = bsum(s, sh);
+// e_c,j = b_j - y_j c_j = max(0, -g_j); S = ||e_c||_1 was formed with g.
+__global__ void __launch_bounds__(kRB) k_round_prep(int64_t n, const double* b, const double* c, const double* g,
+                                                   RoundVecs R, const double* scal) {
+  const int64_t j = gtid();
+  if (j >= n) return;
+  const double s = scal[S_ECSUM];
   const double invS = s > 0.0 ? 1.0 / s : 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) {
-    const double cj = c[j];
-    const double y = fmin(b[j] / cj, 1.0);
-    const double om = fmax(0.0, g[j] / cj);
-    const double ec = fmax(0.0, -g[j]);
-    put2(R.y32, R.y64, j, y);
-    put2(R.om32, R.om64, j, om);
-    put2(R.ec32, R.ec64, j, ec);
-    put2(R.ecs32, R.ecs64, j, ec * invS);
-    R.ecsl32[j] = (float)(ec * invS - (double)(float)(ec * invS));
-    put2(R.lec32, R.lec64, j, log(ec));
-  }
-  if (threadIdx.x == 0) scal[S_ECSUM] = s;
+  const double cj = c[j];
+  const double y = fmin(b[j] / cj, 1.0);
+  const double om = fmax(0.0, g[j] / cj);
+  const double ec = fmax(0.0, -g[j]);
+  put2(R.y32, R.y64, j, y);
+  put2(R.om32, R.om64, j, om);
+  put2(R.ec32, R.ec64, j, ec);
+  put2(R.ecs32, R.ecs64, j, ec * invS);
+  R.ecsl32[j] = (float)(ec * invS - (double)(float)(ec * invS));
+  put2(R.lec32, R.lec64, j, log(ec));
+  put2(R.hom32, R.hom64, j, om > 0.0 ? (1.0 - om) * log1p(-om) + om : 0.0);
 }
 
-// column marginal violation of Xhat and b^T gamma
-__global__ void __launch_bounds__(kVB) k_certify_cols(int64_t n, const double* b, const double* colF, const double* c,
-                                                     const double* gam, double ersum, double* scal) {
-  __shared__ double sh[64];
-  double es = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) es += fmax(0.0, b[j] - c[j]);
-  es = bsum(es, sh);
+// column marginal violation of Xhat and b^T gamma; sum_j max(0, b_j - c_j) = S
+__global__ void __launch_bounds__(kRB) k_certify_cols(int64_t n, const double* b, const double* colF, const double* c,
+                                                     const double* gam, double ersum, double* scal, RedBuf rb) {
+  const double es = scal[S_ECSUM];
   const double f = es > 0.0 ? ersum / es : 0.0;
-  double viol = 0.0, bg = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) {
+  const int64_t j = gtid();
+  double v[2] = {0.0, 0.0};
+  if (j < n) {
     const double ec = fmax(0.0, b[j] - c[j]);
-    viol += fabs(colF[j] + ec * f - b[j]);
-    bg += b[j] * gam[j];
+    v[0] = fabs(colF[j] + ec * f - b[j]);
+    v[1] = b[j] * gam[j];
   }
-  viol = bsum(viol, sh);
-  bg = bsum(bg, sh);
-  if (threadIdx.x == 0) {
-    scal[S_COLVIOL] = viol;
-    scal[S_BGAM] = bg;
+  if (reduce_last<2>(v, 0u, rb)) {
+    scal[S_COLVIOL] = v[0];
+    scal[S_BGAM] = v[1];
   }
 }
 
@@ -284,15 +329,15 @@ __global__ void k_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc
 }
 
 // float copy of gamma and max_j |gamma_j| for the certificate's float32 c-transform scan
-__global__ void __launch_bounds__(kVB) k_certify_prep(int64_t n, const double* gam, float* gam32, double* scal) {
-  __shared__ double sh[kVB / 32];
-  double mx = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kVB) {
+__global__ void __launch_bounds__(kRB) k_certify_prep(int64_t n, const double* gam, float* gam32, double* scal,
+                                                     RedBuf rb) {
+  const int64_t j = gtid();
+  double v[1] = {0.0};
+  if (j < n) {
     gam32[j] = (float)gam[j];
-    mx = fmax(mx, fabs(gam[j]));
+    v[0] = fabs(gam[j]);
   }
-  mx = bmax(mx, sh);
-  if (threadIdx.x == 0) scal[S_GMAX] = mx;
+  if (reduce_last<1>(v, 1u, rb)) scal[S_GMAX] = v[0];
 }
 
 __global__ void k_set_slot(double* scal, int slot, double v) { scal[slot] = v; }
@@ -311,11 +356,13 @@ __global__ void k_neg(int64_t n, const double* x, double* y) {
 
 }  // namespace
 
+static unsigned nblk(int64_t n) { return (unsigned)((n + kRB - 1) / kRB); }
+
 cudaError_t launch_finish_cols(const double* colpart, int nb, int64_t ldk, int64_t n, const double* b,
                                double* c_out, double* g_out, const double* rowpart, int nrp, double* scal,
-                               unsigned int* counter, double* blockbuf, cudaStream_t st) {
-  const int nbk = (int)((n + 255) / 256);
-  k_finish_cols<<<nbk, 256, 0, st>>>(colpart, nb, ldk, n, b, c_out, g_out, rowpart, nrp, scal, counter, blockbuf);
+                               const RedBuf& rb, cudaStream_t st) {
+  k_finish_cols<<<(unsigned)((n + 31) / 32), kRB, 0, st>>>(colpart, nb, ldk, n, b, c_out, g_out, rowpart, nrp, scal,
+                                                          rb);
   note_launch();
   return cudaGetLastError();
 }
@@ -323,50 +370,53 @@ cudaError_t launch_finish_cols(const double* colpart, int nb, int64_t ldk, int64
 cudaError_t launch_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam, double* ganc,
                               const double* logb, double* wv, float* wvh, float* wvl, double* dd, float* d32,
                               double* d64, cudaStream_t st) {
-  k_set_anchor<<<1, kVB, 0, st>>>(n, ldk, eta, Gam, gam, ganc, logb, wv, wvh, wvl, dd, d32, d64);
+  k_set_anchor<<<nblk(ldk), kRB, 0, st>>>(n, ldk, eta, Gam, gam, ganc, logb, wv, wvh, wvl, dd, d32, d64);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_sinkhorn_update(int64_t n, double eta, const double* b, const double* c, double* gam,
                                    const double* ganc, double* dd, float* d32, double* d64, bool fp64,
-                                   double* scal, cudaStream_t st) {
-  k_sinkhorn_update<<<1, kVB, 0, st>>>(n, eta, b, c, gam, ganc, dd, d32, d64, fp64, scal);
+                                   double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_sinkhorn_update<<<nblk(n), kRB, 0, st>>>(n, eta, b, c, gam, ganc, dd, d32, d64, fp64, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_center(int64_t n, double eta, double* gam, const double* ganc, double* dd, float* d32,
-                          double* d64, double* scal, cudaStream_t st) {
-  k_center<<<1, kVB, 0, st>>>(n, eta, gam, ganc, dd, d32, d64, scal);
-  note_launch();
+                          double* d64, double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_sum_into<<<nblk(n), kRB, 0, st>>>(n, gam, scal, S_MEAN, rb);
+  k_center<<<nblk(n), kRB, 0, st>>>(n, eta, gam, ganc, dd, d32, d64, scal, rb);
+  note_launch(2);
   return cudaGetLastError();
 }
-cudaError_t launch_dir_post(int64_t n, double eta, double* delta, const double* g, double* scal, cudaStream_t st) {
-  k_dir_post<<<1, kVB, 0, st>>>(n, eta, delta, g, scal);
-  note_launch();
+cudaError_t launch_dir_post(int64_t n, double eta, double* delta, const double* g, double* scal, const RedBuf& rb,
+                            cudaStream_t st) {
+  k_sum_into<<<nblk(n), kRB, 0, st>>>(n, delta, scal, S_TMP, rb);
+  k_dir_post<<<nblk(n), kRB, 0, st>>>(n, eta, delta, g, scal, rb);
+  note_launch(2);
   return cudaGetLastError();
 }
 cudaError_t launch_armijo_prep(int64_t n, int64_t ldk, double eta, double t, const double* delta, const double* c,
-                               float* em32, double* em64, double* scal, cudaStream_t st) {
-  k_armijo_prep<<<1, kVB, 0, st>>>(n, ldk, eta, t, delta, c, em32, em64, scal);
+                               float* em32, double* em64, double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_armijo_prep<<<nblk(ldk), kRB, 0, st>>>(n, ldk, eta, t, delta, c, em32, em64, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_armijo_accept(int64_t n, double eta, double t, const double* delta, double* gam,
                                  const double* ganc, double* dd, float* d32, double* d64, const double* cnew,
-                                 const double* b, double* g, double* scal, cudaStream_t st) {
-  k_armijo_accept<<<1, kVB, 0, st>>>(n, eta, t, delta, gam, ganc, dd, d32, d64, cnew, b, g, scal);
+                                 const double* b, double* g, double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_armijo_accept<<<nblk(n), kRB, 0, st>>>(n, eta, t, delta, gam, ganc, dd, d32, d64, cnew, b, g, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_round_prep(int64_t n, const double* b, const double* c, const double* g, const RoundVecs& R,
                               double* scal, cudaStream_t st) {
-  k_round_prep<<<1, kVB, 0, st>>>(n, b, c, g, R, scal);
+  k_round_prep<<<nblk(n), kRB, 0, st>>>(n, b, c, g, R, scal);
   note_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_certify_cols(int64_t n, const double* b, const double* colF, const double*, const double* c,
-                                const double* gam, double ersum, double* scal, cudaStream_t st) {
-  k_certify_cols<<<1, kVB, 0, st>>>(n, b, colF, c, gam, ersum, scal);
+cudaError_t launch_certify_cols(int64_t n, const double* b, const double* colF, const double* c, const double* gam,
+                                double ersum, double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_certify_cols<<<nblk(n), kRB, 0, st>>>(n, b, colF, c, gam, ersum, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
@@ -387,8 +437,9 @@ cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ld
   note_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, cudaStream_t st) {
-  k_certify_prep<<<1, kVB, 0, st>>>(n, gam, gam32, scal);
+cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, const RedBuf& rb,
+                                cudaStream_t st) {
+  k_certify_prep<<<nblk(n), kRB, 0, st>>>(n, gam, gam32, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
