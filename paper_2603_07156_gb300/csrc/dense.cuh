@@ -66,6 +66,7 @@ struct DenseArgs {
   const float* wvh;
   const float* wvl;
   float lamh, laml;
+  double* scal;            // slot S_DEVERR records a timed-out wait
 };
 
 template <typename T, int TG, int CH>
@@ -85,6 +86,24 @@ struct Tile {
       if (c < ldk) {
         T kv[V], d[V];
         load_vec_stream(row + c, kv);
+        load_vec(dv + c, d);
+#pragma unroll
+        for (int e = 0; e < V; ++e) x[s][e] = kv[e] + d[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) x[s][e] = neg_inf<T>();
+      }
+    }
+  }
+
+  // x = K_i + d with the row of K in shared memory (float passes)
+  __device__ __forceinline__ void load_smem(const T* row, const T* __restrict__ dv, int64_t ldk) {
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int64_t c = col(s);
+      if (c < ldk) {
+        T kv[V], d[V];
+        load_vec(row + c, kv);
         load_vec(dv + c, d);
 #pragma unroll
         for (int e = 0; e < V; ++e) x[s][e] = kv[e] + d[e];
@@ -178,6 +197,98 @@ __device__ __forceinline__ void row_range(int m, int rpb, int& r0, int& r1) {
   r1 = min(m, r0 + rpb);
 }
 
+// ---------------------------------------------------------------------------
+// Row stream.  Float passes receive the rows of K in shared memory by a bulk
+// asynchronous copy (TMA), issued by one thread and completed on an mbarrier
+// with the transaction byte count; the copy of row i+1 is issued as soon as
+// every thread holds row i in registers, so it runs under the reductions and
+// arithmetic of row i.  Waits are bounded in time: a wait that runs out
+// records scal[S_DEVERR] and the pass returns.  Float64 passes load rows from
+// global memory directly (their shared memory holds the column accumulator).
+// Dynamic shared memory of a float pass: [row buffer, ldk floats][column
+// accumulator of a float-float pass, ldk doubles].
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kRowWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
+  uint32_t spins = 0;
+  unsigned long long t0 = 0;
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((++spins & 255u) == 0) {
+      const unsigned long long now = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kRowWaitNs) {
+        return false;
+      }
+    }
+  }
+}
+
+template <typename T>
+struct RowStream {
+  float* buf = nullptr;
+  uint32_t bar = 0;
+  uint32_t parity = 0;
+
+  __device__ __forceinline__ void issue(const DenseArgs<T>& A, int row) {  // one thread
+    const uint32_t bytes = (uint32_t)(A.ldk * (int64_t)sizeof(float));
+    const float* src = reinterpret_cast<const float*>(A.K) + (int64_t)row * A.ldk;
+    // the block's reads of the previous row (generic proxy) precede this write (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(buf)), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+  }
+
+  // set up the barrier and start the copy of the block's first row
+  __device__ __forceinline__ void start(const DenseArgs<T>& A, double* dyn, unsigned long long* mbar, int r0, int r1) {
+    if constexpr (std::is_same<T, float>::value) {
+      buf = reinterpret_cast<float*>(dyn);
+      bar = smem_u32(mbar);
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (r0 < r1) issue(A, r0);
+      }
+      __syncthreads();
+    }
+  }
+
+  // row i into the tile; starts the copy of row i+1.  False: a wait ran out
+  // (recorded), every thread of the block returns false together.
+  template <int TG, int CH>
+  __device__ __forceinline__ bool row(Tile<T, TG, CH>& t, const DenseArgs<T>& A, int i, int r1) {
+    if constexpr (std::is_same<T, float>::value) {
+      const bool ok = mbar_wait_parity(bar, parity);
+      parity ^= 1u;
+      if (ok) t.load_smem(buf, A.dv, A.ldk);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0 && A.scal != nullptr) A.scal[S_DEVERR] = 1.0;
+        return false;
+      }
+      if (threadIdx.x == 0 && i + 1 < r1) issue(A, i + 1);
+    } else {
+      t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    }
+    return true;
+  }
+};
+
 // Shift subtracted from a row's exponents before exp.  Float32 passes use 0:
 // the anchored K is <= 0 with row maximum 0, the potential offsets d stay
 // within [-16, 16] (the anchor is rebuilt beyond that) and an Armijo trial
@@ -210,7 +321,8 @@ __device__ __forceinline__ void row_sum(T (&v)[K], float* shf) {
 // ---------------------------------------------------------------------------
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
-  extern __shared__ double dyn_sm[];
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
@@ -218,10 +330,12 @@ __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
   acc.init(dyn_sm, A.ldk);
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<T> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   T lpart = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const T mx = row_shift<T, TG, CH>(t, sht);
     T S[1] = {t.exp_shift(mx)};
     row_sum<T, TG, 1>(S, shf);
@@ -266,7 +380,8 @@ __device__ __forceinline__ float psi_log1p_minus(float s) {
 
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
-  extern __shared__ double dyn_sm[];
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
@@ -274,10 +389,12 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
   acc.init(dyn_sm, A.ldk);
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<T> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   T ppsi = T(0), plog = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const T mx = row_shift<T, TG, CH>(t, sht);
     T S[2] = {T(0), T(0)};
 #pragma unroll
@@ -366,17 +483,21 @@ struct StopTau<double> {
 
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   constexpr T tau = StopTau<T>::v;
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<T> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   const T invS = (T)(A.s1 > 0.0 ? 1.0 / A.s1 : 0.0);
   T dpart = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);  // t.x keeps the exponents x_ij
+    if (!rs.row(t, A, i, r1)) return;  // t.x keeps the exponents x_ij
     const T mx = row_shift<T, TG, CH>(t, sht);
     // row sum and sum_j e_ij omega_j in one reduction
     T R[2] = {T(0), T(0)};
@@ -446,6 +567,8 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
 // ---------------------------------------------------------------------------
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   __shared__ int shi[TG / 32];
@@ -458,10 +581,12 @@ __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
     for (int e = 0; e < V; ++e) cnt[s][e] = 0;
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<T> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   const T rho = (T)A.s1;
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const T mx = row_shift<T, TG, CH>(t, sht);
     T S[1] = {t.exp_shift(mx)};
     row_sum<T, TG, 1>(S, shf);
@@ -559,7 +684,8 @@ __device__ __forceinline__ double cost_at(const CostRef& c, int i, int64_t j) {
 // ---------------------------------------------------------------------------
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
-  extern __shared__ double dyn_sm[];
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ double shd[6 * (TG / 32)];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
@@ -568,10 +694,12 @@ __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
   acc.init(dyn_sm, A.ldk);
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<T> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   double part[7] = {0, 0, 0, 0, 0, 0, 0};
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const T mx = row_shift<T, TG, CH>(t, sht);
     double S[1] = {(double)t.exp_shift(mx)};
     block_sum_ff<TG, 1>(S, shf);
@@ -702,14 +830,18 @@ __global__ void __launch_bounds__(TG) k_reanchor(DenseArgs<T> A) {
 // ---------------------------------------------------------------------------
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<T> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const T mx = row_shift<T, TG, CH>(t, sht);
     T S[1] = {t.exp_shift(mx)};
     row_sum<T, TG, 1>(S, shf);
@@ -842,20 +974,23 @@ __global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
 // plan pass: lse_i, c_j = sum_i a_i P_ij, sum_i a_i lse_i (Eqs. 6-7)
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
-  extern __shared__ double dyn_sm[];
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ double s_w;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
-  double* sm = dyn_sm;
+  double* sm = dyn_sm + A.ldk / 2;  // after the row buffer
   for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
   __syncthreads();
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<float> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   double lpart = 0.0;
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
     const double M = (double)mx;
     t.exp_shift(mx);  // float32 filter values
@@ -896,22 +1031,25 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
 // Armijo trial in difference form (see k_armijo); v1d = em_j in float64
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
-  extern __shared__ double dyn_sm[];
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ double s_w;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
-  double* sm = dyn_sm;
+  double* sm = dyn_sm + A.ldk / 2;  // after the row buffer
   for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
   __syncthreads();
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<float> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   double ppsi = 0.0, plog = 0.0;
   // an entry can grow by exp(t max|Delta|/eta) at the trial point: keep more
   const float keep = kFFKeep * (float)A.s2;
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
     const double M = (double)mx;
     t.exp_shift(mx);
@@ -962,7 +1100,8 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
 // certificate (see k_certify): v1d = y, v2d = omega, v3d = e_c / S in float64
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
-  extern __shared__ double dyn_sm[];
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   __shared__ long long shl[TG / 32];
@@ -971,15 +1110,17 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   const float zbound = 2.f * (float)ldexp(A.bounds[0] + A.bounds[1], -22);
   const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
   constexpr int V = 4;
-  double* sm = dyn_sm;
+  double* sm = dyn_sm + A.ldk / 2;  // after the row buffer
   for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
   __syncthreads();
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<float> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   double part[7] = {0, 0, 0, 0, 0, 0, 0};
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
     const double M = (double)mx;
     t.exp_shift(mx);
@@ -1083,15 +1224,19 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
 // plan export for checks
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
+  extern __shared__ __align__(128) double dyn_sm[];
+  __shared__ unsigned long long s_mbar;
   __shared__ double shd[2 * (TG / 32)];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
+  RowStream<float> rs;
+  rs.start(A, dyn_sm, &s_mbar, r0, r1);
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
-    t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
+    if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
     const double M = (double)mx;
     t.exp_shift(mx);

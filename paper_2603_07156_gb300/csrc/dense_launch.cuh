@@ -76,8 +76,13 @@ cudaError_t launch_dense_t(Pass p, DenseArgs<T>& A, int nsm, cudaStream_t st, Pa
   if (q < 0) return cudaErrorInvalidValue;
   const void* fn = kernel_for<T>(q, p);
   const int tg = TileTable<T>::tg[q];
+  // float64 passes: column accumulator; float passes: the row buffer of the row stream
   size_t smem = 0;
-  if (std::is_same<T, double>::value && pass_uses_colacc(p)) smem = (size_t)A.ldk * sizeof(double);
+  if (std::is_same<T, double>::value) {
+    if (pass_uses_colacc(p)) smem = (size_t)A.ldk * sizeof(double);
+  } else if (p != Pass::Reanchor) {
+    smem = (size_t)A.ldk * sizeof(float);
+  }
   // one-time opt-in to large dynamic shared memory, and cached occupancy
   static std::mutex mu;
   static int occ_cache[TileTable<T>::count][(int)Pass::kCount] = {};
@@ -153,7 +158,9 @@ inline cudaError_t launch_dense_ff_t(Pass p, DenseArgs<float>& A, int nsm, cudaS
   const void* fn = ff_kernel_for(q, p);
   if (fn == nullptr) return cudaErrorInvalidValue;
   const int tg = TileTable<float>::tg[q];
-  const size_t smem = (p == Pass::Export || p == Pass::Reanchor) ? 0 : (size_t)A.ldk * sizeof(double);
+  // row buffer of the row stream, then the float64 column accumulator
+  const size_t smem = p == Pass::Reanchor ? 0
+                      : (size_t)A.ldk * sizeof(float) + (p == Pass::Export ? 0 : (size_t)A.ldk * sizeof(double));
   static std::mutex mu;
   static int occ_cache[TileTable<float>::count][(int)Pass::kCount] = {};
   static size_t smem_set[TileTable<float>::count][(int)Pass::kCount] = {};

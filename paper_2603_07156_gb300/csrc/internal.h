@@ -77,6 +77,7 @@ enum Slot : int {
   S_MAXROW = 29, S_MAXCOL = 30,  // longest row / column of P_rho (diagnostics)
   S_CMAX = 31, S_GMAX = 32,      // max C_ij, max_j |gamma_j| (adjacent: certificate bounds)
   S_TMP = 33,                    // scratch total between two kernels of one step
+  S_DEVERR = 34,                 // nonzero: a bounded device wait of a dense pass ran out
   S_NSLOTS = 64
 };
 

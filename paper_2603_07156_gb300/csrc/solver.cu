@@ -266,6 +266,7 @@ int read_scal(ibsn_ctx* X) {
   CK(cudaMemcpyAsync(X->h_scal, X->scal, sizeof(double) * S_NSLOTS, cudaMemcpyDeviceToHost, X->st));
   CK(cudaStreamSynchronize(X->st));
   if (X->prof.on) X->prof.harvest();
+  if (X->h_scal[S_DEVERR] != 0.0) return IBSN_ERR_TIMEOUT;  // a dense pass's bounded wait ran out
   return IBSN_OK;
 }
 
@@ -366,6 +367,7 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
   A.cost = X->cost;
   A.s1 = in.s1;
   A.s2 = in.s2;
+  A.scal = X->scal;
   A.gam32 = X->gam32;
   A.v3lo = X->rv.ecsl32;
   A.bounds = X->scal + S_CMAX;
@@ -707,6 +709,7 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
     delete X;
     return code;
   };
+  if (cudaMemsetAsync(X->scal, 0, sizeof(double) * S_NSLOTS, st) != cudaSuccess) return fail(IBSN_ERR_CUDA);
   // validation (Eq. 1): a, b > 0, finite, sums 1; C finite and >= 0
   if (launch_validate_marginals(pr->m, pr->n, pr->a, pr->b, X->scal, st) != cudaSuccess) return fail(IBSN_ERR_CUDA);
   if (pr->cost_kind != IBSN_COST_GRID2D &&
