@@ -164,6 +164,12 @@ struct PcgBufs {
   int* err;
 };
 
+// PCG on one thread-block cluster (float32 Hessian, m, n <= 16 x 1024): sets
+// *launched when it ran; *err = kDevCapacity afterwards means the staged
+// entries did not fit and nothing was computed.
+cudaError_t launch_pcg_cluster(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, int istar, const float* a32,
+                               double eta, double shift, double rtol, int maxit, double* scal, cudaStream_t st,
+                               bool* launched);
 cudaError_t launch_pcg(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, int istar, bool fp64,
                        const double* a, const float* a32, double eta, double shift, double rtol, int maxit,
                        double timeout_s, int nsm, int64_t nnz, double* scal, cudaStream_t st);

@@ -29,6 +29,8 @@ thread_local std::string g_last_cuda_error;
 
 constexpr double kReanchorF32 = 16.0;   // max |d_j| before a float32 anchor is rebuilt
 constexpr double kReanchorF64 = 1e6;
+// nonzeros up to which a direction is first tried on one thread-block cluster
+constexpr int64_t kClusterPcgMaxNnz = 160000;
 
 struct Carver {
   char* base;
@@ -142,6 +144,8 @@ struct ibsn_ctx {
   double gn = 0.0;         // ||g|| at the current gamma
   int64_t dense_passes = 0;
   int reanchors = 0;
+  int64_t cl_fail_nnz = INT64_MAX;  // smallest nnz whose cluster PCG did not fit
+  int64_t cl_runs = 0;              // directions solved by the cluster PCG
   // device buffers
   float* K32 = nullptr;     // float anchored matrix (hi plane in the polish)
   float* Klo = nullptr;     // lo plane of the float-float anchored matrix
@@ -531,14 +535,37 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
   SparseBufs S = X->sp;
   S.diag = X->c2;
   const bool prof0 = X->prof.on;
-  {
-    ProfScope ps(X, 6, 0.0, X->sp_f64);
-    CK(launch_pcg(S, X->pc, X->m, X->n, X->istar, X->sp_f64, X->a, X->a32, X->eta, shift, rtol, max_cg,
-                  X->prm.wait_timeout_s, X->nsm, X->nnz, X->scal, X->st));
-  }
   int perr = 0;
-  CK(cudaMemcpyAsync(&perr, X->pc.err, sizeof(int), cudaMemcpyDeviceToHost, X->st));
-  RT(read_scal(X));
+  // small float32 systems: one thread-block cluster (no grid-wide waits);
+  // if its shared memory cannot hold the entries, the grid-wide kernel
+  bool done = false;
+  if (!X->sp_f64 && X->nnz <= kClusterPcgMaxNnz && X->nnz < X->cl_fail_nnz) {
+    bool launched = false;
+    {
+      ProfScope ps(X, 6, 0.0, false);
+      CK(launch_pcg_cluster(S, X->pc, X->m, X->n, X->istar, X->a32, X->eta, shift, rtol, max_cg, X->scal, X->st,
+                            &launched));
+    }
+    if (launched) {
+      CK(cudaMemcpyAsync(&perr, X->pc.err, sizeof(int), cudaMemcpyDeviceToHost, X->st));
+      RT(read_scal(X));
+      if (perr == kDevCapacity) {
+        X->cl_fail_nnz = X->nnz;
+      } else {
+        done = true;
+        X->cl_runs++;
+      }
+    }
+  }
+  if (!done) {
+    {
+      ProfScope ps(X, 6, 0.0, X->sp_f64);
+      CK(launch_pcg(S, X->pc, X->m, X->n, X->istar, X->sp_f64, X->a, X->a32, X->eta, shift, rtol, max_cg,
+                    X->prm.wait_timeout_s, X->nsm, X->nnz, X->scal, X->st));
+    }
+    CK(cudaMemcpyAsync(&perr, X->pc.err, sizeof(int), cudaMemcpyDeviceToHost, X->st));
+    RT(read_scal(X));
+  }
   if (perr == kDevTimeout) return IBSN_ERR_TIMEOUT;
   CK(cudaMemcpyAsync(X->delta, X->pc.x, sizeof(double) * X->n, cudaMemcpyDeviceToDevice, X->st));
   CK(launch_dir_post(X->n, X->eta, X->delta, X->g, X->scal, rb(X), X->st));
