@@ -197,6 +197,14 @@ __device__ __forceinline__ FF ff_mul_f(FF x, float y) {
   return ff_fast_two_sum(p, fmaf(x.hi, y, -p) + x.lo * y);
 }
 __device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
+// (a.hi + a.lo) / (b.hi + b.lo) to about 2^-46 relative (one correction step)
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float p = q1 * b.hi;
+  const float pe = fmaf(q1, b.hi, -p);
+  const float r = ((a.hi - p) - pe) + (a.lo - q1 * b.lo);
+  return ff_fast_two_sum(q1, __fdiv_rn(r, b.hi));
+}
 __device__ __forceinline__ FF ff_from(double v) {
   const float hi = (float)v;
   return {hi, (float)(v - (double)hi)};
@@ -238,6 +246,31 @@ __device__ __forceinline__ void block_sum_ff(double (&v)[K], float* sh) {
   }
 }
 
+// Block sum of K float-float values, result on every thread (no float64
+// arithmetic); `sh` holds 2*K*NT/32 floats.
+template <int NT, int K>
+__device__ __forceinline__ void block_sum_ffv(FF (&v)[K], float* sh) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = warp_sum_ff(v[q]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      sh[2 * (q * NW + w)] = v[q].hi;
+      sh[2 * (q * NW + w) + 1] = v[q].lo;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    FF t = lane < NW ? FF{sh[2 * (q * NW + lane)], sh[2 * (q * NW + lane) + 1]} : FF{0.f, 0.f};
+    if constexpr (NW > 1) t = warp_sum_ff(t);
+    v[q] = t;
+  }
+}
+
 // Block sum of K floats (float32 passes, whose accuracy is float32 anyway).
 template <int NT, int K>
 __device__ __forceinline__ void block_sum_f(float (&v)[K], float* sh) {
@@ -257,6 +290,25 @@ __device__ __forceinline__ void block_sum_f(float (&v)[K], float* sh) {
     if constexpr (NW > 1) t = warp_sum(t);
     v[q] = t;
   }
+}
+
+// psi(s) = log1p(s) - s (Armijo difference form)
+__device__ __forceinline__ double psi_log1p_minus(double s) {
+  // log1p(s) - s; Taylor series for small |s| to avoid cancellation
+  if (fabs(s) < 1e-3) {
+    const double s2 = s * s;
+    return s2 * (-0.5 + s * (1.0 / 3.0 + s * (-0.25 + s * (0.2 - s / 6.0))));
+  }
+  return log1p(s) - s;
+}
+__device__ __forceinline__ float psi_log1p_minus(float s) {
+  // float: series sum_{k>=2} (-1)^(k+1) s^k / k to s^10 for |s| < 0.1
+  if (fabsf(s) < 0.1f) {
+    const float s2 = s * s;
+    return s2 * (-0.5f + s * (1.f / 3.f + s * (-0.25f + s * (0.2f + s * (-1.f / 6.f + s * (1.f / 7.f + s * (
+                     -0.125f + s * (1.f / 9.f + s * -0.1f))))))));
+  }
+  return log1pf(s) - s;
 }
 
 // Minimum of a float64 value over a block without float64 arithmetic: doubles

@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "ffmath.cuh"
 #include "internal.h"
 
 namespace ibsn {
@@ -67,6 +68,17 @@ struct DenseArgs {
   const float* wvl;
   float lamh, laml;
   double* scal;            // slot S_DEVERR records a timed-out wait
+  // float-float passes: per-row results for the row kernels, a_i - fl32(a_i)
+  double* rowS0;
+  double* rowS1;
+  double* rowM;
+  const float* alo;
+  double* rowbuf;          // certificate: 6 planes of m per-row results
+  // float-float lo parts of the per-column inputs: d, v1, v2, gamma
+  const float* dvlo;
+  const float* v1lo;
+  const float* v2lo;
+  const float* gamlo;
 };
 
 template <typename T, int TG, int CH>
@@ -174,6 +186,8 @@ struct ColAcc {
       r[s][e].add(v);
     }
   }
+  // float64 partials (float64 passes) or float-float pairs {s, -c} (float
+  // passes: no float64 conversion here; the column finish adds the pairs)
   __device__ __forceinline__ void flush(double* __restrict__ out, int64_t ldk) {
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
@@ -184,7 +198,7 @@ struct ColAcc {
           if constexpr (kSmem) {
             out[c + e] = sm[c + e];
           } else {
-            out[c + e] = r[s][e].value();
+            reinterpret_cast<float2*>(out)[c + e] = make_float2(r[s][e].s, -r[s][e].c);
           }
         }
       }
@@ -360,23 +374,7 @@ __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
 // rowpart[0] = sum_i a_i psi(s_i), psi(s) = log1p(s) - s (second order),
 // rowpart[1] = sum_i a_i log1p(s_i).  rowout = new lse (nullable).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double psi_log1p_minus(double s) {
-  // log1p(s) - s; Taylor series for small |s| to avoid cancellation
-  if (fabs(s) < 1e-3) {
-    const double s2 = s * s;
-    return s2 * (-0.5 + s * (1.0 / 3.0 + s * (-0.25 + s * (0.2 - s / 6.0))));
-  }
-  return log1p(s) - s;
-}
-__device__ __forceinline__ float psi_log1p_minus(float s) {
-  // float: series sum_{k>=2} (-1)^(k+1) s^k / k to s^10 for |s| < 0.1
-  if (fabsf(s) < 0.1f) {
-    const float s2 = s * s;
-    return s2 * (-0.5f + s * (1.f / 3.f + s * (-0.25f + s * (0.2f + s * (-1.f / 6.f + s * (1.f / 7.f + s * (
-                     -0.125f + s * (1.f / 9.f + s * -0.1f))))))));
-  }
-  return log1pf(s) - s;
-}
+// psi_log1p_minus: common.cuh
 
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
@@ -666,8 +664,13 @@ __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
 __device__ __forceinline__ double cost_at(const CostRef& c, int i, int64_t j) {
   if (c.kind == 0) return __ldg(static_cast<const double*>(c.C) + (int64_t)i * c.ldc + j);
   if (c.kind == 1) return (double)__ldg(static_cast<const float*>(c.C) + (int64_t)i * c.ldc + j);
-  const int ri = i / c.gw, ci = i - ri * c.gw;
-  const int rj = (int)j / c.gw, cj = (int)j - rj * c.gw;
+  int ri, ci, rj, cj;
+  if (c.rc != nullptr) {
+    const int pi = __ldg(c.rc + i), pj = __ldg(c.rc + j);
+    ri = pi & 0xffff, ci = pi >> 16, rj = pj & 0xffff, cj = pj >> 16;
+  } else {
+    ri = i / c.gw, ci = i - ri * c.gw, rj = (int)j / c.gw, cj = (int)j - rj * c.gw;
+  }
   const int dr = ri - rj, dc = ci - cj;
   return c.scale * (double)(dr * dr + dc * dc);
 }
@@ -872,7 +875,8 @@ struct FFRow {
   // float64 exponent of entry (s, e) of row i relative to the shift M
   __device__ __forceinline__ static double x64(const DenseArgs<float>& A, int i, int64_t c, int e, double M) {
     const int64_t off = (int64_t)i * A.ldk + c + e;
-    return ((double)__ldg(A.K + off) + (double)__ldg(A.Klo + off)) + A.dv64[c + e] - M;
+    const double lo = A.Klo != nullptr ? (double)__ldg(A.Klo + off) : 0.0;  // no lo plane: float32 K
+    return ((double)__ldg(A.K + off) + lo) + A.dv64[c + e] - M;
   }
 };
 
@@ -886,8 +890,13 @@ __device__ __forceinline__ float2 cost_ff(const CostRef& c, int i, int64_t j, fl
     const float h = (float)C;
     return make_float2(h, (float)(C - (double)h));
   }
-  const int ri = i / c.gw, ci = i - ri * c.gw;
-  const int rj = (int)j / c.gw, cj = (int)j - rj * c.gw;
+  int ri, ci, rj, cj;
+  if (c.rc != nullptr) {
+    const int pi = __ldg(c.rc + i), pj = __ldg(c.rc + j);
+    ri = pi & 0xffff, ci = pi >> 16, rj = pj & 0xffff, cj = pj >> 16;
+  } else {
+    ri = i / c.gw, ci = i - ri * c.gw, rj = (int)j / c.gw, cj = (int)j - rj * c.gw;
+  }
   const float q = (float)((ri - rj) * (ri - rj) + (ci - cj) * (ci - cj));
   const float p = q * sh;
   return make_float2(p, fmaf(q, sl, fmaf(q, sh, -p)));
@@ -971,133 +980,183 @@ __global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
   }
 }
 
-// plan pass: lse_i, c_j = sum_i a_i P_ij, sum_i a_i lse_i (Eqs. 6-7)
+// bit s * V + e set for each entry of the thread's tile above `keep`
+template <int TG, int CH>
+__device__ __forceinline__ unsigned kept_mask(const Tile<float, TG, CH>& t, float keep) {
+  static_assert(CH * 4 <= 32, "one bit per entry of the tile");
+  unsigned mk = 0u;
+#pragma unroll
+  for (int s = 0; s < CH; ++s)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (t.x[s][e] > keep) mk |= 1u << (s * 4 + e);
+  return mk;
+}
+
+// Up to four kept entries of a thread's row tile with their float-float exp,
+// so the second sweep reuses them (entry position s * V + e; -1 = empty); a
+// thread with more kept entries recomputes the rest.
+struct KeptCache {
+  int k0 = -1, k1 = -1, k2 = -1, k3 = -1;
+  FF v0{0.f, 0.f}, v1{0.f, 0.f}, v2{0.f, 0.f}, v3{0.f, 0.f};
+  int n = 0;
+  __device__ __forceinline__ void put(int pos, FF v) {
+    if (n == 0) { k0 = pos; v0 = v; }
+    else if (n == 1) { k1 = pos; v1 = v; }
+    else if (n == 2) { k2 = pos; v2 = v; }
+    else if (n == 3) { k3 = pos; v3 = v; }
+    ++n;
+  }
+  __device__ __forceinline__ bool get(int pos, FF& v) const {
+    if (pos == k0) { v = v0; return true; }
+    if (pos == k1) { v = v1; return true; }
+    if (pos == k2) { v = v2; return true; }
+    if (pos == k3) { v = v3; return true; }
+    return false;
+  }
+};
+
+// float-float exponent x_ij - mx of entry (s, e) of row i: K_hi + K_lo (K_lo
+// absent in float32 mode) + d (hi + lo) - mx
+__device__ __forceinline__ FF ff_x(const DenseArgs<float>& A, int i, int64_t c, int e, float mx) {
+  const int64_t off = (int64_t)i * A.ldk + c + e;
+  const float kl = A.Klo != nullptr ? __ldg(A.Klo + off) : 0.f;
+  const FF x = ff_add(FF{__ldg(A.K + off), kl}, FF{A.dv[c + e], A.dvlo[c + e]});
+  return ff_add(x, FF{-mx, 0.f});
+}
+
+__device__ __forceinline__ FF ff_at(const float* h, const float* l, int64_t j) { return FF{h[j], l[j]}; }
+
+// float64 value as a float-float pair (float64 instructions: kept entries only)
+__device__ __forceinline__ FF ff_of(double v) {
+  const float h = (float)v;
+  return FF{h, (float)(v - (double)h)};
+}
+
+// plan pass: c_j = sum_i a_i P_ij (Eqs. 6-7).  Per-entry work in float-float
+// (no float64 instruction on the per-row path); the pass stores S_i (float2)
+// and the shift M_i (float) per row, and k_rows_ff forms lse_i = M_i + log S_i
+// and sum_i a_i lse_i.  Column partials are float-float pairs.
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
   extern __shared__ __align__(128) double dyn_sm[];
   __shared__ unsigned long long s_mbar;
-  __shared__ double s_w;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
-  double* sm = dyn_sm + A.ldk / 2;  // after the row buffer
-  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
+  float2* acc = reinterpret_cast<float2*>(dyn_sm + A.ldk / 2);  // after the row buffer
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) acc[c] = make_float2(0.f, 0.f);
   __syncthreads();
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<float> rs;
   rs.start(A, dyn_sm, &s_mbar, r0, r1);
-  double lpart = 0.0;
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
-    const double M = (double)mx;
     t.exp_shift(mx);  // float32 filter values
-    double ps = 0.0;
-#pragma unroll
-    for (int s = 0; s < CH; ++s) {
-      const int64_t c = Tile<float, TG, CH>::col(s);
-#pragma unroll
-      for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > kFFKeep) ps += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+    const unsigned kept = kept_mask<TG, CH>(t, kFFKeep);
+    // kept entries: one copy of the float-float code, looped over the mask
+    KeptCache kc;
+    FF S[1] = {FF{0.f, 0.f}};
+    for (unsigned mk = kept; mk != 0u; mk &= mk - 1u) {
+      const int pos = __ffs(mk) - 1;
+      const int64_t c = Tile<float, TG, CH>::col(pos / V);
+      const FF ev = ff_exp(ff_x(A, i, c, pos % V, mx));
+      kc.put(pos, ev);
+      S[0] = ff_add(S[0], ev);
     }
-    double S[1] = {ps};
-    block_sum_ff<TG, 1>(S, shf);
-    // per-row float64 scalars in one thread (float64 throughput is low: the
-    // whole block computing them would cost more than the row's traffic)
+    block_sum_ffv<TG, 1>(S, shf);
     if (threadIdx.x == 0) {
-      const double lse = M + log(S[0]);
-      const double ai = A.a[i];
-      lpart += ai * lse;
-      if (A.rowout != nullptr) A.rowout[i] = lse;
-      s_w = ai / S[0];
+      reinterpret_cast<float2*>(A.rowS0)[i] = make_float2(S[0].hi, S[0].lo);
+      reinterpret_cast<float*>(A.rowM)[i] = mx;
     }
-    __syncthreads();
-    const double w = s_w;
-#pragma unroll
-    for (int s = 0; s < CH; ++s) {
-      const int64_t c = Tile<float, TG, CH>::col(s);
-#pragma unroll
-      for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > kFFKeep) sm[c + e] += w * exp(FFRow<TG, CH>::x64(A, i, c, e, M));
+    if (kept == 0u) continue;  // no kept entry among this thread's columns
+    const FF w = ff_div(FF{A.aT[i], A.alo[i]}, S[0]);
+    for (unsigned mk = kept; mk != 0u; mk &= mk - 1u) {
+      const int pos = __ffs(mk) - 1;
+      const int64_t c = Tile<float, TG, CH>::col(pos / V) + pos % V;
+      FF ev;
+      if (!kc.get(pos, ev)) ev = ff_exp(ff_x(A, i, c - pos % V, pos % V, mx));
+      const float2 a = acc[c];
+      const FF r = ff_add(FF{a.x, a.y}, ff_mul(w, ev));
+      acc[c] = make_float2(r.hi, r.lo);
     }
   }
   __syncthreads();
-  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) A.colpart[(int64_t)blockIdx.x * A.ldk + c] = sm[c];
-  if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = lpart;
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG)
+    reinterpret_cast<float2*>(A.colpart)[(int64_t)blockIdx.x * A.ldk + c] = acc[c];
 }
 
-// Armijo trial in difference form (see k_armijo); v1d = em_j in float64
+// Armijo trial in difference form (see k_armijo); v1 = em_j (hi, lo parts).
+// Stores S0_i, S1_i (float2) and M_i per row for k_rows_ff; the row weight
+// a_i / (S0 + S1) and the column contributions in float-float.
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
   extern __shared__ __align__(128) double dyn_sm[];
   __shared__ unsigned long long s_mbar;
-  __shared__ double s_w;
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
-  double* sm = dyn_sm + A.ldk / 2;  // after the row buffer
-  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
+  float2* acc = reinterpret_cast<float2*>(dyn_sm + A.ldk / 2);
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) acc[c] = make_float2(0.f, 0.f);
   __syncthreads();
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<float> rs;
   rs.start(A, dyn_sm, &s_mbar, r0, r1);
-  double ppsi = 0.0, plog = 0.0;
   // an entry can grow by exp(t max|Delta|/eta) at the trial point: keep more
   const float keep = kFFKeep * (float)A.s2;
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
-    const double M = (double)mx;
     t.exp_shift(mx);
-    double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-    for (int s = 0; s < CH; ++s) {
-      const int64_t c = Tile<float, TG, CH>::col(s);
-#pragma unroll
-      for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > keep) {
-          const double ev = exp(FFRow<TG, CH>::x64(A, i, c, e, M));
-          s0 += ev;
-          s1 += ev * A.v1d[c + e];
-        }
+    const unsigned kept = kept_mask<TG, CH>(t, keep);
+    KeptCache kc;
+    FF S[2] = {FF{0.f, 0.f}, FF{0.f, 0.f}};
+    for (unsigned mk = kept; mk != 0u; mk &= mk - 1u) {
+      const int pos = __ffs(mk) - 1;
+      const int64_t c = Tile<float, TG, CH>::col(pos / V);
+      const FF ev = ff_exp(ff_x(A, i, c, pos % V, mx));
+      kc.put(pos, ev);
+      S[0] = ff_add(S[0], ev);
+      S[1] = ff_add(S[1], ff_mul(ev, ff_at(A.v1, A.v1lo, c + pos % V)));
     }
-    double S[2] = {s0, s1};
-    block_sum_ff<TG, 2>(S, shf);
-    if (threadIdx.x == 0) {  // per-row float64 scalars in one thread
-      const double si = S[1] / S[0];
-      const double ai = A.a[i];
-      const double l1p = log1p(si);
-      ppsi += ai * psi_log1p_minus(si);
-      plog += ai * l1p;
-      if (A.rowout != nullptr) A.rowout[i] = M + log(S[0]) + l1p;
-      s_w = ai / (S[0] * (1.0 + si));
+    block_sum_ffv<TG, 2>(S, shf);
+    if (threadIdx.x == 0) {
+      reinterpret_cast<float2*>(A.rowS0)[i] = make_float2(S[0].hi, S[0].lo);
+      reinterpret_cast<float2*>(A.rowS1)[i] = make_float2(S[1].hi, S[1].lo);
+      reinterpret_cast<float*>(A.rowM)[i] = mx;
     }
-    __syncthreads();
-    const double w = s_w;
-#pragma unroll
-    for (int s = 0; s < CH; ++s) {
-      const int64_t c = Tile<float, TG, CH>::col(s);
-#pragma unroll
-      for (int e = 0; e < V; ++e)
-        if (t.x[s][e] > keep) {
-          const double ev = exp(FFRow<TG, CH>::x64(A, i, c, e, M));
-          sm[c + e] += w * (ev + ev * A.v1d[c + e]);
-        }
+    if (kept == 0u) continue;
+    const FF w = ff_div(FF{A.aT[i], A.alo[i]}, ff_add(S[0], S[1]));
+    for (unsigned mk = kept; mk != 0u; mk &= mk - 1u) {
+      const int pos = __ffs(mk) - 1;
+      const int64_t c = Tile<float, TG, CH>::col(pos / V) + pos % V;
+      FF ev;
+      if (!kc.get(pos, ev)) ev = ff_exp(ff_x(A, i, c - pos % V, pos % V, mx));
+      const FF x = ff_add(ev, ff_mul(ev, ff_at(A.v1, A.v1lo, c)));  // ev (1 + em_j)
+      const float2 a = acc[c];
+      const FF r = ff_add(FF{a.x, a.y}, ff_mul(w, x));
+      acc[c] = make_float2(r.hi, r.lo);
     }
   }
   __syncthreads();
-  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) A.colpart[(int64_t)blockIdx.x * A.ldk + c] = sm[c];
-  if (threadIdx.x == 0) {
-    A.rowpart[blockIdx.x * kRowParts + 0] = ppsi;
-    A.rowpart[blockIdx.x * kRowParts + 1] = plog;
-  }
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG)
+    reinterpret_cast<float2*>(A.colpart)[(int64_t)blockIdx.x * A.ldk + c] = acc[c];
 }
 
-// certificate (see k_certify): v1d = y, v2d = omega, v3d = e_c / S in float64
+// certificate (see k_certify): v1 = y, v2 = omega (hi, lo parts), v3 = e_c / S
+// (hi, v3lo), v1d/v3d float64 copies for the plan export.  Per row: the kept
+// entries' plan values in float-float (cached), zeta_i = min_j C_ij - gamma_j
+// by a float32 scan whose candidates within the float32 error bound of the
+// minimum are re-evaluated exactly in float64, and (dense costs only) the
+// rank-one sum_j C_ij e_c,j / S in float-float; the sums over kept entries in
+// float-float.  k_rows_cert forms the per-row float64 scalars (e_r, primal,
+// dual and residual totals) from the stored per-row results; for the grid cost
+// it forms sum_j C_ij e_c,j / S from four moments of e_c / S.
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   extern __shared__ __align__(128) double dyn_sm[];
@@ -1105,120 +1164,132 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   __shared__ long long shl[TG / 32];
-  __shared__ double s_inv, s_er;
+  __shared__ double s_er;
   // |fl32(C) - fl32(gamma) - (C - gamma)| <= 2^-22 (max|C| + max|gamma|)
   const float zbound = 2.f * (float)ldexp(A.bounds[0] + A.bounds[1], -22);
   const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
+  const bool rank1 = A.cost.kind != 2;  // grid: closed form in k_rows_cert
   constexpr int V = 4;
-  double* sm = dyn_sm + A.ldk / 2;  // after the row buffer
-  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) sm[c] = 0.0;
+  float2* acc = reinterpret_cast<float2*>(dyn_sm + A.ldk / 2);
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) acc[c] = make_float2(0.f, 0.f);
   __syncthreads();
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<float> rs;
   rs.start(A, dyn_sm, &s_mbar, r0, r1);
-  double part[7] = {0, 0, 0, 0, 0, 0, 0};
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
-    const double M = (double)mx;
     t.exp_shift(mx);
-    const double ai = A.a[i];
-    // sweep 1: row sum (float64, kept entries); zeta_i = min_j C_ij - gamma_j by a
-    // float32 scan whose candidates (within the float32 error bound of the
-    // minimum) are re-evaluated exactly; sum_j C_ij e_c,j / S in float-float
-    // (all terms >= 0); sum C^2 in float32 (it only scales Delta_kkt)
-    double s0 = 0.0;
-    float z32 = __builtin_huge_valf(), c2f = 0.f, ceh = 0.f, cel = 0.f;
+    // sweep 1 (every entry, float32): c-transform scan and, for dense costs,
+    // the rank-one sum; the kept entries' float-float work runs from the mask
+    const unsigned kept = kept_mask<TG, CH>(t, kFFKeep);
+    float z32 = __builtin_huge_valf(), ceh = 0.f, cel = 0.f;
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         if (c + e >= A.n) continue;
-        if (t.x[s][e] > kFFKeep) s0 += exp(FFRow<TG, CH>::x64(A, i, c, e, M));
         const float2 C = cost_ff(A.cost, i, c + e, csh, csl);
         z32 = fminf(z32, C.x - A.gam32[c + e]);
-        c2f = fmaf(C.x, C.x, c2f);
-        // C e_c / S in float-float: exact product of the hi parts plus the cross terms
-        const float vh = A.v3[c + e];
-        const float p = C.x * vh;
-        cel += fmaf(C.x, A.v3lo[c + e], fmaf(C.y, vh, fmaf(C.x, vh, -p)));
-        ff_acc(ceh, cel, p);
+        if (rank1) {
+          // C e_c / S in float-float: exact product of the hi parts plus the cross terms
+          const float vh = A.v3[c + e];
+          const float p = C.x * vh;
+          cel += fmaf(C.x, A.v3lo[c + e], fmaf(C.y, vh, fmaf(C.x, vh, -p)));
+          ff_acc(ceh, cel, p);
+        }
       }
     }
-    double R[3] = {s0, (double)c2f, (double)ceh + (double)cel};
-    block_sum_ff<TG, 3>(R, shf);
+    KeptCache kc;
+    FF R[2] = {FF{0.f, 0.f}, ff_fast_two_sum(ceh, cel)};
+    for (unsigned mk = kept; mk != 0u; mk &= mk - 1u) {
+      const int pos = __ffs(mk) - 1;
+      const FF ev = ff_exp(ff_x(A, i, Tile<float, TG, CH>::col(pos / V), pos % V, mx));
+      kc.put(pos, ev);
+      R[0] = ff_add(R[0], ev);
+    }
+    block_sum_ffv<TG, 2>(R, shf);
     const float m32 = -block_max<TG>(-z32, sht);
     double zc = kInf;
-#pragma unroll
-    for (int s = 0; s < CH; ++s) {
-      const int64_t c = Tile<float, TG, CH>::col(s);
-#pragma unroll
-      for (int e = 0; e < V; ++e) {
-        if (c + e >= A.n) continue;
-        if (cost_ff(A.cost, i, c + e, csh, csl).x - A.gam32[c + e] <= m32 + zbound)
-          zc = fmin(zc, cost_at(A.cost, i, c + e) - A.gam[c + e]);
-      }
-    }
-    const double zeta = block_min_exact<TG>(zc, shl);
-    if (threadIdx.x == 0) s_inv = 1.0 / R[0];
-    __syncthreads();
-    const double invS0 = s_inv;
-    // sweep 2: e_r, the plan part of the primal, complementarity, column sums
-    double pom = 0.0, psum = 0.0, pr = 0.0, cu = 0.0;
-#pragma unroll
-    for (int s = 0; s < CH; ++s) {
-      const int64_t c = Tile<float, TG, CH>::col(s);
-#pragma unroll
-      for (int e = 0; e < V; ++e) {
-        if (c + e >= A.n || !(t.x[s][e] > kFFKeep)) continue;
-        const double P = exp(FFRow<TG, CH>::x64(A, i, c, e, M)) * invS0;
-        const double C = cost_at(A.cost, i, c + e);
-        const double F = ai * P * A.v1d[c + e];
-        psum += P;
-        pom += P * A.v2d[c + e];
-        pr += C * F;
-        cu += ai * P * (C - zeta - A.gam[c + e]);
-        sm[c + e] += F;
-      }
-    }
-    double Q[4] = {pom, psum, pr, cu};
-    block_sum_ff<TG, 4>(Q, shf);
-    if (threadIdx.x == 0) {  // per-row float64 scalars in one thread
-      const double er = ai * Q[0];
-      const double rv = ai * (Q[1] - 1.0);
-      part[0] += Q[2] + er * R[2];
-      part[1] += ai * zeta;
-      part[2] += fabs(rv);
-      part[3] += er;
-      part[4] += Q[3];
-      part[5] += R[1];
-      part[6] += rv * rv;
-      if (A.rowout != nullptr) A.rowout[i] = zeta;
-      if (A.rowout2 != nullptr) A.rowout2[i] = er;
-      s_er = er;
-    }
-    if (A.plan_out != nullptr) {
-      __syncthreads();
-      const double er = s_er;
+    if (z32 <= m32 + zbound) {  // only threads holding a candidate: mark, then re-evaluate in float64
+      unsigned cand = 0u;
 #pragma unroll
       for (int s = 0; s < CH; ++s) {
         const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-          if (c + e >= A.n) continue;
-          const double P = t.x[s][e] > kFFKeep ? exp(FFRow<TG, CH>::x64(A, i, c, e, M)) * invS0 : 0.0;
-          A.plan_out[(int64_t)i * A.n + c + e] = ai * P * A.v1d[c + e] + er * A.v3d[c + e];
+        for (int e = 0; e < V; ++e)
+          if (c + e < A.n && cost_ff(A.cost, i, c + e, csh, csl).x - A.gam32[c + e] <= m32 + zbound)
+            cand |= 1u << (s * V + e);
+      }
+      for (; cand != 0u; cand &= cand - 1u) {
+        const int pos = __ffs(cand) - 1;
+        const int64_t j = Tile<float, TG, CH>::col(pos / V) + pos % V;
+        zc = fmin(zc, cost_at(A.cost, i, j) - A.gam[j]);
+      }
+    }
+    const double zeta = block_min_exact<TG>(zc, shl);
+    // sweep 2 (kept entries): e_r, the plan part of the primal, complementarity, column sums
+    FF Q[4] = {FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}};
+    if (kept != 0u) {
+      const FF inv = ff_div(FF{1.f, 0.f}, R[0]);
+      const FF ai{A.aT[i], A.alo[i]};
+      const FF zf = ff_of(zeta);
+      for (unsigned mk = kept; mk != 0u; mk &= mk - 1u) {
+        const int pos = __ffs(mk) - 1;
+        const int64_t c = Tile<float, TG, CH>::col(pos / V) + pos % V;
+        FF ev;
+        if (!kc.get(pos, ev)) ev = ff_exp(ff_x(A, i, c - pos % V, pos % V, mx));
+        const FF P = ff_mul(ev, inv);
+        const float2 Cp = cost_ff(A.cost, i, c, csh, csl);
+        const FF C{Cp.x, Cp.y};
+        const FF aP = ff_mul(ai, P);
+        const FF F = ff_mul(aP, ff_at(A.v1, A.v1lo, c));
+        Q[0] = ff_add(Q[0], ff_mul(P, ff_at(A.v2, A.v2lo, c)));
+        Q[1] = ff_add(Q[1], P);
+        Q[2] = ff_add(Q[2], ff_mul(C, F));
+        const FF red = ff_add(ff_add(C, ff_neg(zf)), ff_neg(ff_at(A.gam32, A.gamlo, c)));
+        Q[3] = ff_add(Q[3], ff_mul(aP, red));
+        const float2 a = acc[c];
+        const FF r = ff_add(FF{a.x, a.y}, F);
+        acc[c] = make_float2(r.hi, r.lo);
+      }
+    }
+    block_sum_ffv<TG, 4>(Q, shf);
+    if (threadIdx.x == 0) {
+      float2* rb2 = reinterpret_cast<float2*>(A.rowbuf);
+      const int64_t m = A.m;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rb2[q * m + i] = make_float2(Q[q].hi, Q[q].lo);
+      A.rowbuf[4 * m + i] = zeta;
+      rb2[5 * m + i] = make_float2(R[1].hi, R[1].lo);
+    }
+    if (A.plan_out != nullptr) {  // the final export: Xhat row by row (float64)
+      if (threadIdx.x == 0) s_er = A.a[i] * ((double)Q[0].hi + (double)Q[0].lo);
+      __syncthreads();
+      const double er = s_er;
+      const FF inv = ff_div(FF{1.f, 0.f}, R[0]);
+      const double a_i = A.a[i];
+#pragma unroll 1
+      for (int pos = 0; pos < CH * V; ++pos) {
+        const int64_t c = Tile<float, TG, CH>::col(pos / V) + pos % V;
+        if (c >= A.n) continue;
+        double P = 0.0;
+        if ((kept >> pos) & 1u) {
+          FF ev;
+          if (!kc.get(pos, ev)) ev = ff_exp(ff_x(A, i, c - pos % V, pos % V, mx));
+          const FF Pf = ff_mul(ev, inv);
+          P = (double)Pf.hi + (double)Pf.lo;
         }
+        A.plan_out[(int64_t)i * A.n + c] = a_i * P * A.v1d[c] + er * A.v3d[c];
       }
     }
   }
   __syncthreads();
-  for (int64_t c = threadIdx.x; c < A.ldk; c += TG) A.colpart[(int64_t)blockIdx.x * A.ldk + c] = sm[c];
-  if (threadIdx.x == 0)
-    for (int q = 0; q < 7; ++q) A.rowpart[blockIdx.x * kRowParts + q] = part[q];
+  for (int64_t c = threadIdx.x; c < A.ldk; c += TG)
+    reinterpret_cast<float2*>(A.colpart)[(int64_t)blockIdx.x * A.ldk + c] = acc[c];
 }
 
 // plan export for checks

@@ -22,6 +22,7 @@ struct CostRef {
   int kind;      // ibsn_cost_kind
   int gw;        // grid width (GRID2D)
   double scale;  // GRID2D scale
+  const int* rc; // GRID2D: bin coordinates packed as row | col << 16 (n entries), or null
 };
 
 enum class Pass : int { Plan = 0, Armijo, Stop, Sparsify, Certify, Reanchor, Export, kCount };
@@ -35,6 +36,7 @@ struct PassGeom {
   int nb = 0;           // blocks
   int rpb = 0;          // rows per block
   size_t smem = 0;      // dynamic shared memory
+  bool ffpart = false;  // column partials are float-float pairs (float passes)
 };
 
 // Leading dimension of the anchored matrix: n rounded up to 32 elements.
@@ -78,6 +80,8 @@ enum Slot : int {
   S_CMAX = 31, S_GMAX = 32,      // max C_ij, max_j |gamma_j| (adjacent: certificate bounds)
   S_TMP = 33,                    // scratch total between two kernels of one step
   S_DEVERR = 34,                 // nonzero: a bounded device wait of a dense pass ran out
+  S_W0 = 40,                     // .. S_W0 + 3: moments of w = e_c / S over the grid (sum w, sum r w, sum c w, sum (r^2 + c^2) w)
+  S_C2SUM = 44,                  // sum_ij C_ij^2 (once per context)
   S_NSLOTS = 64
 };
 
@@ -90,44 +94,52 @@ struct RedBuf {
   unsigned int* counter;
   double* blockbuf;
 };
-cudaError_t launch_finish_cols(const double* colpart, int nb, int64_t ldk, int64_t n, const double* b,
+cudaError_t launch_finish_cols(const double* colpart, bool ffpart, int nb, int64_t ldk, int64_t n, const double* b,
                                double* c_out, double* g_out, const double* rowpart, int nrp, double* scal,
                                const RedBuf& rb, cudaStream_t st);
 
 // single-block vector kernels; `dT` is float or double per `fp64`
+cudaError_t launch_rows_ff(int64_t m, bool armijo, const double* a, const double* S0, const double* S1,
+                           const double* M, double* rowout, double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam, double* ganc,
                               const double* logb, double* wv, float* wvh, float* wvl, double* dd, float* d32,
-                              double* d64, cudaStream_t st);
+                              float* dlo, double* d64, cudaStream_t st);
 cudaError_t launch_sinkhorn_update(int64_t n, double eta, const double* b, const double* c, double* gam,
-                                   const double* ganc, double* dd, float* d32, double* d64, bool fp64,
+                                   const double* ganc, double* dd, float* d32, float* dlo, double* d64, bool fp64,
                                    double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_center(int64_t n, double eta, double* gam, const double* ganc, double* dd, float* d32,
-                          double* d64, double* scal, const RedBuf& rb, cudaStream_t st);
+                          float* dlo, double* d64, double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_dir_post(int64_t n, double eta, double* delta, const double* g, double* scal, const RedBuf& rb,
                             cudaStream_t st);
 cudaError_t launch_armijo_prep(int64_t n, int64_t ldk, double eta, double t, const double* delta, const double* c,
-                               float* em32, double* em64, double* scal, const RedBuf& rb, cudaStream_t st);
+                               float* em32, float* emlo, double* em64, double* scal, const RedBuf& rb,
+                               cudaStream_t st);
 cudaError_t launch_armijo_accept(int64_t n, double eta, double t, const double* delta, double* gam,
-                                 const double* ganc, double* dd, float* d32, double* d64, const double* cnew,
-                                 const double* b, double* g, double* scal, const RedBuf& rb, cudaStream_t st);
+                                 const double* ganc, double* dd, float* d32, float* dlo, double* d64,
+                                 const double* cnew, const double* b, double* g, double* scal, const RedBuf& rb,
+                                 cudaStream_t st);
 // per-column rounding inputs, written in float and float64: y, omega, e_c, e_c / S
 struct RoundVecs {
   float *y32, *om32, *ec32, *ecs32, *lec32;
   float* ecsl32;  // e_c / S - fl32(e_c / S): the float-float lo part
+  float *ylo32, *omlo32;  // lo parts of y and omega
   float* hom32;   // (1 - omega) log(1 - omega) + omega
   double* hom64;
   double *y64, *om64, *ec64, *ecs64, *lec64;  // lec = log e_c (-inf where e_c = 0)
 };
 cudaError_t launch_round_prep(int64_t n, const double* b, const double* c, const double* g, const RoundVecs& R,
-                              double* scal, cudaStream_t st);
+                              const int* grid_rc, double* scal, const RedBuf& rb, cudaStream_t st);
+cudaError_t launch_grid_rc(int64_t n, int gw, int* rc, cudaStream_t st);
+cudaError_t launch_rows_cert(int64_t m, const double* a, const double* rowbuf, const int* grid_rc, double scale,
+                             double* zeta_out, double* er_out, double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_certify_cols(int64_t n, const double* b, const double* colF, const double* c, const double* gam,
                                 double ersum, double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_validate_marginals(int64_t m, int64_t n, const double* a, const double* b, double* scal,
                                       cudaStream_t st);
 cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal,
                                  cudaStream_t st);
-cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, const RedBuf& rb,
-                                cudaStream_t st);
+cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, float* gamlo, double* scal,
+                                const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_set_slot(double* scal, int slot, double v, cudaStream_t st);
 cudaError_t launch_fill_pad(void* v, int64_t n, int64_t ldk, bool fp64, double value, cudaStream_t st);
 cudaError_t launch_neg(int64_t n, const double* x, double* y, cudaStream_t st);

@@ -52,6 +52,10 @@ __global__ void k_to_float(int64_t n, const double* x, float* y) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) y[j] = (float)x[j];
 }
+__global__ void k_lo_float(int64_t n, const double* x, float* y) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) y[j] = (float)(x[j] - (double)(float)x[j]);
+}
 __global__ void k_axpy(int64_t n, double alpha, const double* x, double* y) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) y[j] += alpha * x[j];
@@ -152,7 +156,12 @@ struct ibsn_ctx {
   double* K64 = nullptr;    // float64 anchored matrix (plain float64 mode)
   double *Gam, *gam, *ganc, *dd, *c, *c2, *g, *delta, *logb, *wv, *colF;
   double *lse, *lse2, *er, *zeta;
+  double *rowS0, *rowS1, *rowM;  // per-row results of the float-float passes
+  double* rowbuf;                // 6 x m per-row results of the float-float certificate
+  int* gridrc;                   // grid cost: bin coordinates per column (null otherwise)
+  float* alo32;                  // a - fl32(a)
   float *d32, *em32, *a32, *gam32, *wvh, *wvl;
+  float *dlo32, *emlo32, *gamlo32;  // float-float lo parts
   double *d64, *em64;
   RoundVecs rv{};
   double *colpart, *rowpart, *blockbuf;
@@ -225,18 +234,22 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   X->K64 = X->have_f64 ? cv.take<double>((size_t)m * ldk) : nullptr;
   double** nvec[] = {&X->Gam, &X->gam, &X->ganc, &X->dd, &X->c, &X->c2, &X->g, &X->delta, &X->logb, &X->wv, &X->colF};
   for (double** v : nvec) *v = cv.take<double>(n);
-  double** mvec[] = {&X->lse, &X->lse2, &X->er, &X->zeta};
+  double** mvec[] = {&X->lse, &X->lse2, &X->er, &X->zeta, &X->rowS0, &X->rowS1, &X->rowM};
   for (double** v : mvec) *v = cv.take<double>(m);
   X->a32 = cv.take<float>(m);
+  X->alo32 = cv.take<float>(m);
+  X->rowbuf = cv.take<double>(6 * (size_t)m);
+  X->gridrc = pr->cost_kind == IBSN_COST_GRID2D ? cv.take<int>(n) : nullptr;
   float** fvec[] = {&X->d32,      &X->em32,      &X->gam32,      &X->rv.y32,   &X->rv.om32, &X->rv.ec32,
-                    &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32, &X->wvh,      &X->wvl, &X->rv.hom32};
+                    &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32, &X->wvh,      &X->wvl, &X->rv.hom32,
+                    &X->dlo32,    &X->emlo32,    &X->gamlo32,    &X->rv.ylo32, &X->rv.omlo32};
   for (float** v : fvec) *v = cv.take<float>(ldk);
   double** dvec[] = {&X->d64,       &X->em64,       &X->rv.y64,     &X->rv.om64,
                      &X->rv.ec64,   &X->rv.ecs64,   &X->rv.lec64,   &X->rv.hom64};
   for (double** v : dvec) *v = cv.take<double>(ldk);
   X->colpart = cv.take<double>((size_t)nbcap * ldk);
   X->rowpart = cv.take<double>((size_t)nbcap * kRowParts);
-  X->blockbuf = cv.take<double>(4 * ((n + 31) / 32) + 8);
+  X->blockbuf = cv.take<double>(8 * std::max((n + 31) / 32, (m + 255) / 256) + 8);
   X->sp.pool_col = cv.take<int32_t>(cap);
   X->sp.pool_val = cv.take<double>(cap);
   X->sp.row_start = cv.take<int64_t>(m);
@@ -312,7 +325,9 @@ enum class Mode { F32, F64, FF };
 
 Mode mode_for(const ibsn_ctx* X, Pass p) {
   if (X->prec == 0) return Mode::F64;
-  if (X->prec == 1) return Mode::F32;
+  // the certificate uses the float-float kernel in both float modes (without
+  // a lo plane in float32 mode: the entries are then those of float32 K)
+  if (X->prec == 1) return p == Pass::Certify ? Mode::FF : Mode::F32;
   // float-float polish: the passes that produce the gradient, the Armijo
   // decrease and the certificate are float64-accurate; the Hessian model
   // (sparsify) and the stop test read the float hi plane
@@ -323,6 +338,7 @@ Mode mode_for(const ibsn_ctx* X, Pass p) {
 // Inputs of one dense pass beyond the common ones.
 struct PassIn {
   const float *v1f = nullptr, *v2f = nullptr, *v3f = nullptr, *v4f = nullptr;
+  const float *v1lo = nullptr, *v2lo = nullptr;
   const double *v1d = nullptr, *v2d = nullptr, *v3d = nullptr, *v4d = nullptr;
   double s1 = 0.0, s2 = 0.0;
   double *rowout = nullptr, *rowout2 = nullptr, *plan_out = nullptr;
@@ -356,7 +372,7 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
   } else {
     A.aT = X->a;
   }
-  A.Klo = X->Klo;
+  A.Klo = X->prec == 2 ? X->Klo : nullptr;  // the lo plane is maintained in the polish only
   A.dv64 = X->d64;
   A.v1d = in.v1d;
   A.v2d = in.v2d;
@@ -372,6 +388,15 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
   A.s1 = in.s1;
   A.s2 = in.s2;
   A.scal = X->scal;
+  A.rowS0 = X->rowS0;
+  A.rowS1 = X->rowS1;
+  A.rowM = X->rowM;
+  A.alo = X->alo32;
+  A.rowbuf = X->rowbuf;
+  A.dvlo = X->dlo32;
+  A.v1lo = in.v1lo;
+  A.v2lo = in.v2lo;
+  A.gamlo = X->gamlo32;
   A.gam32 = X->gam32;
   A.v3lo = X->rv.ecsl32;
   A.bounds = X->scal + S_CMAX;
@@ -423,6 +448,7 @@ double pass_bytes(ibsn_ctx* X, Pass p, Mode md) {
 int run_pass(ibsn_ctx* X, Pass p, const PassIn& in, PassGeom* g = nullptr) {
   // the float anchor is built in float-float arithmetic (K32, and Klo in the polish)
   const Mode md = p == Pass::Reanchor ? (X->prec == 0 ? Mode::F64 : Mode::FF) : mode_for(X, p);
+  if (g) g->ffpart = md != Mode::F64;  // float passes write float-float column partials
   ProfScope ps(X, pass_kind(p), pass_bytes(X, p, md), md != Mode::F32);
   if (md == Mode::F64) {
     DenseArgs<double> A = make_args<double>(X, in);
@@ -438,7 +464,7 @@ int run_pass(ibsn_ctx* X, Pass p, const PassIn& in, PassGeom* g = nullptr) {
 
 // finish a pass that wrote column partials: c_out = sum of partials, g = c - b
 int finish(ibsn_ctx* X, const PassGeom& g, double* c_out, bool grad, int nrp) {
-  CK(launch_finish_cols(X->colpart, g.nb, X->ldk, X->n, grad ? X->b : nullptr, c_out, grad ? X->g : nullptr,
+  CK(launch_finish_cols(X->colpart, g.ffpart, g.nb, X->ldk, X->n, grad ? X->b : nullptr, c_out, grad ? X->g : nullptr,
                         X->rowpart, nrp, X->scal, rb(X), X->st));
   return IBSN_OK;
 }
@@ -448,7 +474,7 @@ int finish(ibsn_ctx* X, const PassGeom& g, double* c_out, bool grad, int nrp) {
 // a1: anchor build for the current (k, Gamma, gamma) in precision X->prec
 int do_reanchor(ibsn_ctx* X) {
   CK(launch_set_anchor(X->n, X->ldk, X->eta, X->Gam, X->gam, X->ganc, X->logb, X->wv, X->wvh, X->wvl, X->dd,
-                       X->d32, X->d64, X->st));
+                       X->d32, X->dlo32, X->d64, X->st));
   PassIn in;
   in.reanchor = true;
   in.lam = (double)(X->k + 1) / X->eta;
@@ -469,14 +495,19 @@ int do_plan(ibsn_ctx* X) {
   PassIn in;
   in.rowout = X->lse;
   RT(run_pass(X, Pass::Plan, in, &g));
-  RT(finish(X, g, X->c, true, 1));
+  if (mode_for(X, Pass::Plan) == Mode::FF) {
+    CK(launch_rows_ff(X->m, false, X->a, X->rowS0, nullptr, X->rowM, X->lse, X->scal, rb(X), X->st));
+    RT(finish(X, g, X->c, true, 0));
+  } else {
+    RT(finish(X, g, X->c, true, 1));
+  }
   RT(read_scal(X));
   X->gn = std::sqrt(X->h_scal[S_GN2]);
   return IBSN_OK;
 }
 
 int do_center(ibsn_ctx* X) {
-  CK(launch_center(X->n, X->eta, X->gam, X->ganc, X->dd, X->d32, X->d64, X->scal, rb(X), X->st));
+  CK(launch_center(X->n, X->eta, X->gam, X->ganc, X->dd, X->d32, X->dlo32, X->d64, X->scal, rb(X), X->st));
   return IBSN_OK;
 }
 
@@ -485,7 +516,7 @@ int do_sinkhorn(ibsn_ctx* X, double tol, int max_iter, int* iters) {
   RT(do_plan(X));
   int it = 0;
   while (X->gn >= tol && it < max_iter) {
-    CK(launch_sinkhorn_update(X->n, X->eta, X->b, X->c, X->gam, X->ganc, X->dd, X->d32, X->d64, X->prec == 0,
+    CK(launch_sinkhorn_update(X->n, X->eta, X->b, X->c, X->gam, X->ganc, X->dd, X->d32, X->dlo32, X->d64, X->prec == 0,
                               X->scal, rb(X), X->st));
     RT(read_scal(X));
     RT(maybe_reanchor(X, X->h_scal[S_DMAX]));
@@ -584,18 +615,25 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
 
 // a6: one Armijo trial; dL = t g^T Delta + eta sum_j c_j phi_j + eta sum_i a_i psi(s_i)
 int do_armijo_trial(ibsn_ctx* X, double t, double* dL, double* slope) {
-  CK(launch_armijo_prep(X->n, X->ldk, X->eta, t, X->delta, X->c, X->em32, X->em64, X->scal, rb(X), X->st));
+  CK(launch_armijo_prep(X->n, X->ldk, X->eta, t, X->delta, X->c, X->em32, X->emlo32, X->em64, X->scal, rb(X),
+                        X->st));
   PassGeom g;
   PassIn in;
   in.v1f = X->em32;
   in.v1d = X->em64;
+  in.v1lo = X->emlo32;
   in.rowout = X->lse2;
   // entry j moves by t Delta_j / eta at the trial point, so its ratio to the
   // row maximum can grow by exp(2 t max|Delta| / eta): the float-float filter
   // keeps entries above 2^-64 exp(-2 t max|Delta| / eta) of the anchor maximum
   in.s2 = std::exp(-2.0 * t * X->h_scal[S_DELTAMAX]);
   RT(run_pass(X, Pass::Armijo, in, &g));
-  RT(finish(X, g, X->c2, false, 2));
+  if (mode_for(X, Pass::Armijo) == Mode::FF) {
+    CK(launch_rows_ff(X->m, true, X->a, X->rowS0, X->rowS1, X->rowM, X->lse2, X->scal, rb(X), X->st));
+    RT(finish(X, g, X->c2, false, 0));
+  } else {
+    RT(finish(X, g, X->c2, false, 2));
+  }
   RT(read_scal(X));
   const double sl = X->h_scal[S_SLOPE];
   *slope = sl;
@@ -604,8 +642,8 @@ int do_armijo_trial(ibsn_ctx* X, double t, double* dL, double* slope) {
 }
 
 int do_accept(ibsn_ctx* X, double t) {
-  CK(launch_armijo_accept(X->n, X->eta, t, X->delta, X->gam, X->ganc, X->dd, X->d32, X->d64, X->c2, X->b, X->g,
-                          X->scal, rb(X), X->st));
+  CK(launch_armijo_accept(X->n, X->eta, t, X->delta, X->gam, X->ganc, X->dd, X->d32, X->dlo32, X->d64, X->c2, X->b,
+                          X->g, X->scal, rb(X), X->st));
   std::swap(X->c, X->c2);
   std::swap(X->lse, X->lse2);
   RT(read_scal(X));
@@ -616,7 +654,7 @@ int do_accept(ibsn_ctx* X, double t) {
 
 // a7: D_phi(Proj(X), X) (Eq. 8) at the current gamma (uses c, g of the current plan)
 int do_stop(ibsn_ctx* X, double* dphi) {
-  CK(launch_round_prep(X->n, X->b, X->c, X->g, X->rv, X->scal, X->st));
+  CK(launch_round_prep(X->n, X->b, X->c, X->g, X->rv, X->gridrc, X->scal, rb(X), X->st));
   RT(read_scal(X));
   PassGeom g;
   PassIn in;
@@ -645,22 +683,31 @@ struct Cert {
 // a8: certificate at X = diag(a) P^k(gamma): primal of the Alg. 3 rounding,
 // c-transform dual, relative gap, marginal violation, Delta_kkt
 int do_certify(ibsn_ctx* X, Cert* out, double* plan, double* zeta) {
-  CK(launch_round_prep(X->n, X->b, X->c, X->g, X->rv, X->scal, X->st));
+  CK(launch_round_prep(X->n, X->b, X->c, X->g, X->rv, X->gridrc, X->scal, rb(X), X->st));
   PassGeom g;
   PassIn in;
   in.v1f = X->rv.y32;
   in.v1d = X->rv.y64;
+  in.v1lo = X->rv.ylo32;
   in.v2f = X->rv.om32;
   in.v2d = X->rv.om64;
+  in.v2lo = X->rv.omlo32;
   in.v3f = X->rv.ecs32;
   in.v3d = X->rv.ecs64;
   in.gam = X->gam;
   in.rowout = zeta ? zeta : X->zeta;
   in.rowout2 = X->er;
   in.plan_out = plan;
-  if (mode_for(X, Pass::Certify) == Mode::FF) CK(launch_certify_prep(X->n, X->gam, X->gam32, X->scal, rb(X), X->st));
+  if (mode_for(X, Pass::Certify) == Mode::FF)
+    CK(launch_certify_prep(X->n, X->gam, X->gam32, X->gamlo32, X->scal, rb(X), X->st));
   RT(run_pass(X, Pass::Certify, in, &g));
-  RT(finish(X, g, X->colF, false, 7));
+  if (mode_for(X, Pass::Certify) == Mode::FF) {
+    CK(launch_rows_cert(X->m, X->a, X->rowbuf, X->gridrc, X->cost.scale, in.rowout, in.rowout2, X->scal, rb(X),
+                        X->st));
+    RT(finish(X, g, X->colF, false, 0));
+  } else {
+    RT(finish(X, g, X->colF, false, 7));
+  }
   RT(read_scal(X));
   const double ersum = X->h_scal[S_ROW0 + 3];
   const double primal = X->h_scal[S_ROW0 + 0];
@@ -719,6 +766,7 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   X->cost.kind = pr->cost_kind;
   X->cost.gw = pr->grid_w;
   X->cost.scale = pr->cost_scale;
+  X->cost.rc = X->gridrc;
   X->a = pr->a;
   X->b = pr->b;
   X->eta = pr->eta;
@@ -743,10 +791,20 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
       launch_validate_cost(pr->m, pr->n, pr->C, pr->ldc, pr->cost_kind, X->scal, st) != cudaSuccess)
     return fail(IBSN_ERR_CUDA);
   if (pr->cost_kind == IBSN_COST_GRID2D) {
-    // max C of the grid cost: the two opposite corners
+    // max C of the grid cost (two opposite corners) and sum C^2 over all pairs
+    // of bins, sum over offsets (dr, dc) of (h - |dr|)(w - |dc|)(dr^2 + dc^2)^2
     const double dh = (double)(pr->grid_h - 1), dw = (double)(pr->grid_w - 1);
+    double c2 = 0.0;
+    for (int dr = -(pr->grid_h - 1); dr < pr->grid_h; ++dr)
+      for (int dc = -(pr->grid_w - 1); dc < pr->grid_w; ++dc) {
+        const double q = (double)dr * dr + (double)dc * dc;
+        c2 += (double)(pr->grid_h - std::abs(dr)) * (double)(pr->grid_w - std::abs(dc)) * q * q;
+      }
+    c2 *= pr->cost_scale * pr->cost_scale;
     if (cudaMemsetAsync(&X->scal[S_CBAD], 0, sizeof(double), st) != cudaSuccess ||
-        launch_set_slot(X->scal, S_CMAX, pr->cost_scale * (dh * dh + dw * dw), st) != cudaSuccess)
+        launch_set_slot(X->scal, S_CMAX, pr->cost_scale * (dh * dh + dw * dw), st) != cudaSuccess ||
+        launch_set_slot(X->scal, S_C2SUM, c2, st) != cudaSuccess ||
+        launch_grid_rc(pr->n, pr->grid_w, X->gridrc, st) != cudaSuccess)
       return fail(IBSN_ERR_CUDA);
   }
   if (read_scal(X) != IBSN_OK) return fail(IBSN_ERR_CUDA);
@@ -770,13 +828,15 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   X->bnorm = std::sqrt(X->bnorm);
   k_log<<<(unsigned)((X->n + 255) / 256), 256, 0, st>>>(X->n, pr->b, X->logb);
   k_to_float<<<(unsigned)((X->m + 255) / 256), 256, 0, st>>>(X->m, pr->a, X->a32);
-  note_launch(2);
+  k_lo_float<<<(unsigned)((X->m + 255) / 256), 256, 0, st>>>(X->m, pr->a, X->alo32);
+  note_launch(3);
   // zero state, pad the float/double per-column vectors
   cudaMemsetAsync(X->Gam, 0, sizeof(double) * X->n, st);
   cudaMemsetAsync(X->gam, 0, sizeof(double) * X->n, st);
   cudaMemsetAsync(X->ctr, 0, sizeof(unsigned int) * C_NCOUNTERS, st);
-  float* tf[] = {X->d32,      X->em32,      X->gam32,      X->rv.y32,   X->rv.om32,
-                 X->rv.ec32, X->rv.ecs32, X->rv.ecsl32, X->rv.lec32, X->rv.hom32};
+  float* tf[] = {X->d32,      X->em32,       X->gam32,    X->rv.y32,  X->rv.om32,   X->rv.ec32,
+                 X->rv.ecs32, X->rv.ecsl32, X->rv.lec32, X->rv.hom32, X->dlo32,    X->emlo32,
+                 X->gamlo32,  X->rv.ylo32,  X->rv.omlo32};
   for (float* v : tf) cudaMemsetAsync(v, 0, sizeof(float) * X->ldk, st);
   double* td[] = {X->d64, X->em64, X->rv.y64, X->rv.om64, X->rv.ec64, X->rv.ecs64, X->rv.lec64, X->rv.hom64};
   for (double* v : td) cudaMemsetAsync(v, 0, sizeof(double) * X->ldk, st);

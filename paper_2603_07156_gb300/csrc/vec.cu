@@ -16,6 +16,13 @@ __device__ __forceinline__ void put2(float* f, double* d, int64_t j, double x) {
   if (f) f[j] = (float)x;
   if (d) d[j] = x;
 }
+// ... and to the float-float lo part x - fl32(x) (may be null)
+__device__ __forceinline__ void put3(float* f, float* lo, double* d, int64_t j, double x) {
+  const float h = (float)x;
+  if (f) f[j] = h;
+  if (lo) lo[j] = (float)(x - (double)h);
+  if (d) d[j] = x;
+}
 
 // block-wide sum / max over kVB threads, result on every thread
 __device__ __forceinline__ double bsum(double v, double* sh) {
@@ -86,16 +93,27 @@ __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * kRB + t
 // g = c - b, ||g||^2 and ||max(0, -g)||_1 (the rounding's S), and the totals of
 // the first nrp row partials.  A block handles 32 columns x 8 slices of the
 // partials; the slices are added in slice order.
-__global__ void __launch_bounds__(kRB) k_finish_cols(const double* __restrict__ colpart, int nb, int64_t ldk,
-                                                     int64_t n, const double* __restrict__ b, double* c_out,
-                                                     double* g_out, const double* __restrict__ rowpart, int nrp,
-                                                     double* scal, RedBuf rb) {
+__global__ void __launch_bounds__(kRB) k_finish_cols(const double* __restrict__ colpart, bool ffpart, int nb,
+                                                     int64_t ldk, int64_t n, const double* __restrict__ b,
+                                                     double* c_out, double* g_out, const double* __restrict__ rowpart,
+                                                     int nrp, double* scal, RedBuf rb) {
   __shared__ double part[8][33];
   const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
   const int64_t j = (int64_t)blockIdx.x * 32 + lane;
   double c = 0.0;
-  if (j < n)
-    for (int q = sl; q < nb; q += 8) c += colpart[(int64_t)q * ldk + j];
+  if (j < n) {
+    if (ffpart) {  // float-float partials of the float passes: added in float-float
+      const float2* p2 = reinterpret_cast<const float2*>(colpart);
+      FF s{0.f, 0.f};
+      for (int q = sl; q < nb; q += 8) {
+        const float2 v = p2[(int64_t)q * ldk + j];
+        s = ff_add(s, FF{v.x, v.y});
+      }
+      c = (double)s.hi + (double)s.lo;
+    } else {
+      for (int q = sl; q < nb; q += 8) c += colpart[(int64_t)q * ldk + j];
+    }
+  }
   part[sl][lane] = c;
   __syncthreads();
   double v[2] = {0.0, 0.0};
@@ -124,10 +142,46 @@ __global__ void __launch_bounds__(kRB) k_finish_cols(const double* __restrict__ 
   }
 }
 
+// Row scalars of the float-float plan and Armijo passes (which store S_i, M_i
+// per row instead of forming float64 logs on their serial per-row path).
+// plan:   lse_i = M_i + log S0_i -> rowout; sum_i a_i lse_i -> scal[S_ROW0]
+// Armijo: s_i = S1_i / S0_i; rowout = M_i + log S0_i + log1p(s_i);
+//         sum_i a_i psi(s_i) -> scal[S_ROW0], sum_i a_i log1p(s_i) -> scal[S_ROW0 + 1]
+__global__ void __launch_bounds__(kRB) k_rows_ff(int64_t m, bool armijo, const double* a, const double* S0,
+                                                const double* S1, const double* M, double* rowout, double* scal,
+                                                RedBuf rb) {
+  const int64_t i = gtid();
+  double v[2] = {0.0, 0.0};
+  if (i < m) {
+    // the passes store S0, S1 as float-float pairs and M as a float
+    const float2 s0 = reinterpret_cast<const float2*>(S0)[i];
+    const double S0i = (double)s0.x + (double)s0.y;
+    const double Mi = (double)reinterpret_cast<const float*>(M)[i];
+    const double ls = log(S0i);
+    if (armijo) {
+      const float2 s1 = reinterpret_cast<const float2*>(S1)[i];
+      const double si = ((double)s1.x + (double)s1.y) / S0i;
+      const double l1p = log1p(si);
+      v[0] = a[i] * psi_log1p_minus(si);
+      v[1] = a[i] * l1p;
+      if (rowout) rowout[i] = Mi + ls + l1p;
+    } else {
+      const double lse = Mi + ls;
+      v[0] = a[i] * lse;
+      if (rowout) rowout[i] = lse;
+    }
+  }
+  if (reduce_last<2>(v, 0u, rb)) {
+    scal[S_ROW0] = v[0];
+    if (armijo) scal[S_ROW0 + 1] = v[1];
+  }
+}
+
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRB) k_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam,
                                                    double* gam, double* ganc, const double* logb, double* wv,
-                                                   float* wvh, float* wvl, double* dd, float* d32, double* d64) {
+                                                   float* wvh, float* wvl, double* dd, float* d32, float* dlo,
+                                                   double* d64) {
   const int64_t j = gtid();
   if (j < n) {
     const double G = (Gam ? Gam[j] : 0.0);
@@ -139,12 +193,12 @@ __global__ void __launch_bounds__(kRB) k_set_anchor(int64_t n, int64_t ldk, doub
     wvl[j] = (float)(w - (double)h);
     dd[j] = 0.0;
   }
-  if (j < ldk) put2(d32, d64, j, 0.0);
+  if (j < ldk) put3(d32, dlo, d64, j, 0.0);
 }
 
 __global__ void __launch_bounds__(kRB) k_sinkhorn_update(int64_t n, double eta, const double* b, const double* c,
                                                         double* gam, const double* ganc, double* dd, float* d32,
-                                                        double* d64, bool fp64, double* scal, RedBuf rb) {
+                                                        float* dlo, double* d64, bool fp64, double* scal, RedBuf rb) {
   const int64_t j = gtid();
   double v[1] = {0.0};
   if (j < n) {
@@ -154,7 +208,7 @@ __global__ void __launch_bounds__(kRB) k_sinkhorn_update(int64_t n, double eta, 
     gam[j] = gj;
     const double d = (gj - ganc[j]) / eta;
     dd[j] = d;
-    put2(d32, d64, j, d);
+    put3(d32, dlo, d64, j, d);
     v[0] = fabs(d);
   }
   if (reduce_last<1>(v, 1u, rb)) scal[S_DMAX] = v[0];
@@ -168,7 +222,7 @@ __global__ void __launch_bounds__(kRB) k_sum_into(int64_t n, const double* x, do
 }
 
 __global__ void __launch_bounds__(kRB) k_center(int64_t n, double eta, double* gam, const double* ganc, double* dd,
-                                               float* d32, double* d64, double* scal, RedBuf rb) {
+                                               float* d32, float* dlo, double* d64, double* scal, RedBuf rb) {
   const double mean = scal[S_MEAN] / (double)n;
   const int64_t j = gtid();
   double v[1] = {0.0};
@@ -177,7 +231,7 @@ __global__ void __launch_bounds__(kRB) k_center(int64_t n, double eta, double* g
     gam[j] = gj;
     const double d = (gj - ganc[j]) / eta;
     dd[j] = d;
-    put2(d32, d64, j, d);
+    put3(d32, dlo, d64, j, d);
     v[0] = fabs(d);
   }
   if (reduce_last<1>(v, 1u, rb)) {
@@ -210,24 +264,24 @@ __device__ __forceinline__ double phi_expm1_minus(double x) {
 }
 
 __global__ void __launch_bounds__(kRB) k_armijo_prep(int64_t n, int64_t ldk, double eta, double t, const double* delta,
-                                                    const double* c, float* em32, double* em64, double* scal,
-                                                    RedBuf rb) {
+                                                    const double* c, float* em32, float* emlo, double* em64,
+                                                    double* scal, RedBuf rb) {
   const int64_t j = gtid();
   double v[1] = {0.0};
   if (j < n) {
     const double x = t * delta[j] / eta;
-    put2(em32, em64, j, expm1(x));
+    put3(em32, emlo, em64, j, expm1(x));
     v[0] = c[j] * phi_expm1_minus(x);
   } else if (j < ldk) {
-    put2(em32, em64, j, 0.0);
+    put3(em32, emlo, em64, j, 0.0);
   }
   if (reduce_last<1>(v, 0u, rb)) scal[S_PHI] = v[0];
 }
 
 __global__ void __launch_bounds__(kRB) k_armijo_accept(int64_t n, double eta, double t, const double* delta,
                                                       double* gam, const double* ganc, double* dd, float* d32,
-                                                      double* d64, const double* cnew, const double* b, double* g,
-                                                      double* scal, RedBuf rb) {
+                                                      float* dlo, double* d64, const double* cnew, const double* b,
+                                                      double* g, double* scal, RedBuf rb) {
   const int64_t j = gtid();
   double v[3] = {0.0, 0.0, 0.0};
   if (j < n) {
@@ -235,7 +289,7 @@ __global__ void __launch_bounds__(kRB) k_armijo_accept(int64_t n, double eta, do
     gam[j] = gj;
     const double d = (gj - ganc[j]) / eta;
     dd[j] = d;
-    put2(d32, d64, j, d);
+    put3(d32, dlo, d64, j, d);
     const double gr = cnew[j] - b[j];
     g[j] = gr;
     v[0] = fabs(d);
@@ -250,24 +304,93 @@ __global__ void __launch_bounds__(kRB) k_armijo_accept(int64_t n, double eta, do
 }
 
 // Alg. 3 with z = 1: y_j = min(b_j/c_j, 1), omega_j = 1 - y_j = max(0, g_j/c_j),
-// e_c,j = b_j - y_j c_j = max(0, -g_j); S = ||e_c||_1 was formed with g.
+// e_c,j = b_j - y_j c_j = max(0, -g_j); S = ||e_c||_1 was formed with g.  For
+// the grid cost also the moments of w = e_c / S that give sum_j C_ij w_j in
+// closed form per row (S_W0 .. S_W0 + 3).
 __global__ void __launch_bounds__(kRB) k_round_prep(int64_t n, const double* b, const double* c, const double* g,
-                                                   RoundVecs R, const double* scal) {
+                                                   RoundVecs R, const int* rc, double* scal, RedBuf rb) {
   const int64_t j = gtid();
-  if (j >= n) return;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
   const double s = scal[S_ECSUM];
   const double invS = s > 0.0 ? 1.0 / s : 0.0;
-  const double cj = c[j];
-  const double y = fmin(b[j] / cj, 1.0);
-  const double om = fmax(0.0, g[j] / cj);
-  const double ec = fmax(0.0, -g[j]);
-  put2(R.y32, R.y64, j, y);
-  put2(R.om32, R.om64, j, om);
-  put2(R.ec32, R.ec64, j, ec);
-  put2(R.ecs32, R.ecs64, j, ec * invS);
-  R.ecsl32[j] = (float)(ec * invS - (double)(float)(ec * invS));
-  put2(R.lec32, R.lec64, j, log(ec));
-  put2(R.hom32, R.hom64, j, om > 0.0 ? (1.0 - om) * log1p(-om) + om : 0.0);
+  if (j < n) {
+    const double cj = c[j];
+    const double y = fmin(b[j] / cj, 1.0);
+    const double om = fmax(0.0, g[j] / cj);
+    const double ec = fmax(0.0, -g[j]);
+    const double w = ec * invS;
+    put3(R.y32, R.ylo32, R.y64, j, y);
+    put3(R.om32, R.omlo32, R.om64, j, om);
+    put2(R.ec32, R.ec64, j, ec);
+    put2(R.ecs32, R.ecs64, j, w);
+    R.ecsl32[j] = (float)(w - (double)(float)w);
+    put2(R.lec32, R.lec64, j, log(ec));
+    put2(R.hom32, R.hom64, j, om > 0.0 ? (1.0 - om) * log1p(-om) + om : 0.0);
+    if (rc) {
+      const double r = (double)(rc[j] & 0xffff), q = (double)(rc[j] >> 16);
+      v[0] = w;
+      v[1] = r * w;
+      v[2] = q * w;
+      v[3] = (r * r + q * q) * w;
+    }
+  }
+  if (rc == nullptr) return;
+  if (reduce_last<4>(v, 0u, rb))
+    for (int q = 0; q < 4; ++q) scal[S_W0 + q] = v[q];
+}
+
+// bin coordinates of the grid cost, packed row | col << 16
+__global__ void k_grid_rc(int64_t n, int gw, int* rc) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    const int r = (int)(j / gw), q = (int)(j - (int64_t)r * gw);
+    rc[j] = r | (q << 16);
+  }
+}
+
+// Row scalars of the float-float certificate pass from its per-row results
+// rowbuf = [sum_j P_ij omega_j | sum_j P_ij | sum_j C_ij a_i P_ij y_j |
+//           a_i sum_j P_ij (C_ij - zeta_i - gamma_j) | zeta_i | sum_j C_ij e_c,j / S]
+// (the last is formed here for the grid cost from the moments S_W0..).
+// e_r,i = a_i Q0, row residual a_i (Q1 - 1); totals into S_ROW0 + 0..6 as the
+// single-pass certificate writes them (slot 5: sum C^2, formed once per context).
+__global__ void __launch_bounds__(kRB) k_rows_cert(int64_t m, const double* a, const double* rb_, const int* rc,
+                                                  double scale, double* zeta_out, double* er_out, double* scal,
+                                                  RedBuf rb) {
+  const int64_t i = gtid();
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (i < m) {
+    const double ai = a[i];
+    const float2* f2 = reinterpret_cast<const float2*>(rb_);  // float-float planes 0..3 and 5
+    auto plane = [&](int q) { const float2 v = f2[q * m + i]; return (double)v.x + (double)v.y; };
+    const double q0 = plane(0), q1 = plane(1), q2 = plane(2), q3 = plane(3), zeta = rb_[4 * m + i];
+    double cw;
+    if (rc) {
+      const double r = (double)(rc[i] & 0xffff), q = (double)(rc[i] >> 16);
+      cw = scale * ((r * r + q * q) * scal[S_W0] - 2.0 * (r * scal[S_W0 + 1] + q * scal[S_W0 + 2]) + scal[S_W0 + 3]);
+    } else {
+      cw = plane(5);
+    }
+    const double er = ai * q0;
+    const double rv = ai * (q1 - 1.0);
+    v[0] = q2 + er * cw;
+    v[1] = ai * zeta;
+    v[2] = fabs(rv);
+    v[3] = er;
+    v[4] = q3;
+    v[5] = rv * rv;
+    if (zeta_out) zeta_out[i] = zeta;
+    if (er_out) er_out[i] = er;
+  }
+  if (reduce_last<6>(v, 0u, rb)) {
+    scal[S_ROW0 + 0] = v[0];
+    scal[S_ROW0 + 1] = v[1];
+    scal[S_ROW0 + 2] = v[2];
+    scal[S_ROW0 + 3] = v[3];
+    scal[S_ROW0 + 4] = v[4];
+    scal[S_ROW0 + 5] = scal[S_C2SUM];
+    scal[S_ROW0 + 6] = v[5];
+  }
 }
 
 // column marginal violation of Xhat and b^T gamma; sum_j max(0, b_j - c_j) = S
@@ -313,28 +436,31 @@ __global__ void __launch_bounds__(kVB) k_validate_marginals(int64_t m, int64_t n
 
 __global__ void k_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal) {
   unsigned int bad = 0;
-  double cmax = 0.0;
+  double cmax = 0.0, c2 = 0.0;
   const int64_t total = m * n;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / n, j = q - i * n;
     const double v = kind == 0 ? static_cast<const double*>(C)[i * ldc + j]
                                : (double)static_cast<const float*>(C)[i * ldc + j];
     if (!(v >= 0.0) || !isfinite(v)) ++bad;
-    else cmax = fmax(cmax, v);
+    else { cmax = fmax(cmax, v); c2 += v * v; }
   }
   bad = (unsigned)warp_sum((int)bad);
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&scal[S_CBAD], (double)bad);
+  // sum C^2 (normalises Delta_kkt only: the summation order is not fixed)
+  c2 = warp_sum(c2);
+  if ((threadIdx.x & 31) == 0 && c2 > 0.0) atomicAdd(&scal[S_C2SUM], c2);
   // non-negative doubles order like their bit patterns
   atomicMax(reinterpret_cast<unsigned long long*>(&scal[S_CMAX]), (unsigned long long)__double_as_longlong(cmax));
 }
 
 // float copy of gamma and max_j |gamma_j| for the certificate's float32 c-transform scan
-__global__ void __launch_bounds__(kRB) k_certify_prep(int64_t n, const double* gam, float* gam32, double* scal,
-                                                     RedBuf rb) {
+__global__ void __launch_bounds__(kRB) k_certify_prep(int64_t n, const double* gam, float* gam32, float* gamlo,
+                                                     double* scal, RedBuf rb) {
   const int64_t j = gtid();
   double v[1] = {0.0};
   if (j < n) {
-    gam32[j] = (float)gam[j];
+    put3(gam32, gamlo, nullptr, j, gam[j]);
     v[0] = fabs(gam[j]);
   }
   if (reduce_last<1>(v, 1u, rb)) scal[S_GMAX] = v[0];
@@ -358,33 +484,40 @@ __global__ void k_neg(int64_t n, const double* x, double* y) {
 
 static unsigned nblk(int64_t n) { return (unsigned)((n + kRB - 1) / kRB); }
 
-cudaError_t launch_finish_cols(const double* colpart, int nb, int64_t ldk, int64_t n, const double* b,
+cudaError_t launch_rows_ff(int64_t m, bool armijo, const double* a, const double* S0, const double* S1,
+                           const double* M, double* rowout, double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_rows_ff<<<nblk(m), kRB, 0, st>>>(m, armijo, a, S0, S1, M, rowout, scal, rb);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_cols(const double* colpart, bool ffpart, int nb, int64_t ldk, int64_t n, const double* b,
                                double* c_out, double* g_out, const double* rowpart, int nrp, double* scal,
                                const RedBuf& rb, cudaStream_t st) {
-  k_finish_cols<<<(unsigned)((n + 31) / 32), kRB, 0, st>>>(colpart, nb, ldk, n, b, c_out, g_out, rowpart, nrp, scal,
-                                                          rb);
+  k_finish_cols<<<(unsigned)((n + 31) / 32), kRB, 0, st>>>(colpart, ffpart, nb, ldk, n, b, c_out, g_out, rowpart, nrp,
+                                                          scal, rb);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_anchor(int64_t n, int64_t ldk, double eta, const double* Gam, double* gam, double* ganc,
                               const double* logb, double* wv, float* wvh, float* wvl, double* dd, float* d32,
-                              double* d64, cudaStream_t st) {
-  k_set_anchor<<<nblk(ldk), kRB, 0, st>>>(n, ldk, eta, Gam, gam, ganc, logb, wv, wvh, wvl, dd, d32, d64);
+                              float* dlo, double* d64, cudaStream_t st) {
+  k_set_anchor<<<nblk(ldk), kRB, 0, st>>>(n, ldk, eta, Gam, gam, ganc, logb, wv, wvh, wvl, dd, d32, dlo, d64);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_sinkhorn_update(int64_t n, double eta, const double* b, const double* c, double* gam,
-                                   const double* ganc, double* dd, float* d32, double* d64, bool fp64,
+                                   const double* ganc, double* dd, float* d32, float* dlo, double* d64, bool fp64,
                                    double* scal, const RedBuf& rb, cudaStream_t st) {
-  k_sinkhorn_update<<<nblk(n), kRB, 0, st>>>(n, eta, b, c, gam, ganc, dd, d32, d64, fp64, scal, rb);
+  k_sinkhorn_update<<<nblk(n), kRB, 0, st>>>(n, eta, b, c, gam, ganc, dd, d32, dlo, d64, fp64, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_center(int64_t n, double eta, double* gam, const double* ganc, double* dd, float* d32,
-                          double* d64, double* scal, const RedBuf& rb, cudaStream_t st) {
+                          float* dlo, double* d64, double* scal, const RedBuf& rb, cudaStream_t st) {
   k_sum_into<<<nblk(n), kRB, 0, st>>>(n, gam, scal, S_MEAN, rb);
-  k_center<<<nblk(n), kRB, 0, st>>>(n, eta, gam, ganc, dd, d32, d64, scal, rb);
+  k_center<<<nblk(n), kRB, 0, st>>>(n, eta, gam, ganc, dd, d32, dlo, d64, scal, rb);
   note_launch(2);
   return cudaGetLastError();
 }
@@ -396,21 +529,34 @@ cudaError_t launch_dir_post(int64_t n, double eta, double* delta, const double* 
   return cudaGetLastError();
 }
 cudaError_t launch_armijo_prep(int64_t n, int64_t ldk, double eta, double t, const double* delta, const double* c,
-                               float* em32, double* em64, double* scal, const RedBuf& rb, cudaStream_t st) {
-  k_armijo_prep<<<nblk(ldk), kRB, 0, st>>>(n, ldk, eta, t, delta, c, em32, em64, scal, rb);
+                               float* em32, float* emlo, double* em64, double* scal, const RedBuf& rb,
+                               cudaStream_t st) {
+  k_armijo_prep<<<nblk(ldk), kRB, 0, st>>>(n, ldk, eta, t, delta, c, em32, emlo, em64, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_armijo_accept(int64_t n, double eta, double t, const double* delta, double* gam,
-                                 const double* ganc, double* dd, float* d32, double* d64, const double* cnew,
-                                 const double* b, double* g, double* scal, const RedBuf& rb, cudaStream_t st) {
-  k_armijo_accept<<<nblk(n), kRB, 0, st>>>(n, eta, t, delta, gam, ganc, dd, d32, d64, cnew, b, g, scal, rb);
+                                 const double* ganc, double* dd, float* d32, float* dlo, double* d64,
+                                 const double* cnew, const double* b, double* g, double* scal, const RedBuf& rb,
+                                 cudaStream_t st) {
+  k_armijo_accept<<<nblk(n), kRB, 0, st>>>(n, eta, t, delta, gam, ganc, dd, d32, dlo, d64, cnew, b, g, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_round_prep(int64_t n, const double* b, const double* c, const double* g, const RoundVecs& R,
-                              double* scal, cudaStream_t st) {
-  k_round_prep<<<nblk(n), kRB, 0, st>>>(n, b, c, g, R, scal);
+                              const int* grid_rc, double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_round_prep<<<nblk(n), kRB, 0, st>>>(n, b, c, g, R, grid_rc, scal, rb);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_grid_rc(int64_t n, int gw, int* rc, cudaStream_t st) {
+  k_grid_rc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, gw, rc);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_rows_cert(int64_t m, const double* a, const double* rowbuf, const int* grid_rc, double scale,
+                             double* zeta_out, double* er_out, double* scal, const RedBuf& rb, cudaStream_t st) {
+  k_rows_cert<<<nblk(m), kRB, 0, st>>>(m, a, rowbuf, grid_rc, scale, zeta_out, er_out, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
@@ -432,14 +578,16 @@ cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ld
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(&scal[S_CMAX], 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&scal[S_C2SUM], 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
   if (kind != 0 && kind != 1) return cudaSuccess;
   k_validate_cost<<<1216, 256, 0, st>>>(m, n, C, ldc, kind, scal);
   note_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, double* scal, const RedBuf& rb,
-                                cudaStream_t st) {
-  k_certify_prep<<<nblk(n), kRB, 0, st>>>(n, gam, gam32, scal, rb);
+cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, float* gamlo, double* scal,
+                                const RedBuf& rb, cudaStream_t st) {
+  k_certify_prep<<<nblk(n), kRB, 0, st>>>(n, gam, gam32, gamlo, scal, rb);
   note_launch();
   return cudaGetLastError();
 }
