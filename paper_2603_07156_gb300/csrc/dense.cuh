@@ -902,6 +902,15 @@ __device__ __forceinline__ float2 cost_ff(const CostRef& c, int i, int64_t j, fl
   return make_float2(p, fmaf(q, sl, fmaf(q, sh, -p)));
 }
 
+// The cost accessors specialised on the cost kind (a template argument of the
+// passes that read C for every entry, so each instantiation holds one kind's code).
+template <int KIND>
+__device__ __forceinline__ CostRef kind_ref(const CostRef& c) {
+  CostRef r = c;
+  r.kind = KIND;
+  return r;
+}
+
 // s += x (float-float, TwoSum)
 __device__ __forceinline__ void ff_acc(float& sh, float& sl, float x) {
   const float t = sh + x;
@@ -922,8 +931,9 @@ constexpr float kFFLoBand = 144.f;
 // lo plane Klo = fl32(K - K32) must carry float64 accuracy for every entry
 // the float-float passes can keep, so those entries (K > -kFFLoBand) are
 // re-evaluated in float64; the rest keep the float-float lo part.
-template <int TG, int CH>
+template <int TG, int CH, int KIND>
 __global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
+  const CostRef cost = kind_ref<KIND>(A.cost);
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
   const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
@@ -938,7 +948,7 @@ __global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         if (c + e < A.n) {
-          const float2 C = cost_ff(A.cost, i, c + e, csh, csl);
+          const float2 C = cost_ff(cost, i, c + e, csh, csl);
           const float p = A.lamh * C.x;  // lam C = p + pl (TwoProduct of the hi parts)
           const float pl = fmaf(A.lamh, C.x, -p) + fmaf(A.lamh, C.y, A.laml * C.x);
           const FF d = ff_add(FF{__ldg(A.wvh + c + e), __ldg(A.wvl + c + e)}, FF{-p, -pl});
@@ -964,7 +974,7 @@ __global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
             kv[e] = k.hi;
             lo[e] = k.lo;
             if (A.Klo_out != nullptr && k.hi > -kFFLoBand) {
-              const double K64 = (A.wv[c + e] - A.lam * cost_at(A.cost, i, c + e)) - (double)mx;
+              const double K64 = (A.wv[c + e] - A.lam * cost_at(cost, i, c + e)) - (double)mx;
               kv[e] = (float)K64;
               lo[e] = (float)(K64 - (double)kv[e]);
             }
@@ -1157,8 +1167,9 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
 // float-float.  k_rows_cert forms the per-row float64 scalars (e_r, primal,
 // dual and residual totals) from the stored per-row results; for the grid cost
 // it forms sum_j C_ij e_c,j / S from four moments of e_c / S.
-template <int TG, int CH>
+template <int TG, int CH, int KIND>
 __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
+  const CostRef cost = kind_ref<KIND>(A.cost);  // the kind is a compile-time constant below
   extern __shared__ __align__(128) double dyn_sm[];
   __shared__ unsigned long long s_mbar;
   __shared__ float shf[8 * (TG / 32)];
@@ -1168,7 +1179,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   // |fl32(C) - fl32(gamma) - (C - gamma)| <= 2^-22 (max|C| + max|gamma|)
   const float zbound = 2.f * (float)ldexp(A.bounds[0] + A.bounds[1], -22);
   const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
-  const bool rank1 = A.cost.kind != 2;  // grid: closed form in k_rows_cert
+  constexpr bool rank1 = KIND != 2;  // grid: closed form in k_rows_cert
   constexpr int V = 4;
   float2* acc = reinterpret_cast<float2*>(dyn_sm + A.ldk / 2);
   for (int64_t c = threadIdx.x; c < A.ldk; c += TG) acc[c] = make_float2(0.f, 0.f);
@@ -1192,7 +1203,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         if (c + e >= A.n) continue;
-        const float2 C = cost_ff(A.cost, i, c + e, csh, csl);
+        const float2 C = cost_ff(cost, i, c + e, csh, csl);
         z32 = fminf(z32, C.x - A.gam32[c + e]);
         if (rank1) {
           // C e_c / S in float-float: exact product of the hi parts plus the cross terms
@@ -1221,13 +1232,13 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
         const int64_t c = Tile<float, TG, CH>::col(s);
 #pragma unroll
         for (int e = 0; e < V; ++e)
-          if (c + e < A.n && cost_ff(A.cost, i, c + e, csh, csl).x - A.gam32[c + e] <= m32 + zbound)
+          if (c + e < A.n && cost_ff(cost, i, c + e, csh, csl).x - A.gam32[c + e] <= m32 + zbound)
             cand |= 1u << (s * V + e);
       }
       for (; cand != 0u; cand &= cand - 1u) {
         const int pos = __ffs(cand) - 1;
         const int64_t j = Tile<float, TG, CH>::col(pos / V) + pos % V;
-        zc = fmin(zc, cost_at(A.cost, i, j) - A.gam[j]);
+        zc = fmin(zc, cost_at(cost, i, j) - A.gam[j]);
       }
     }
     const double zeta = block_min_exact<TG>(zc, shl);
@@ -1243,7 +1254,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
         FF ev;
         if (!kc.get(pos, ev)) ev = ff_exp(ff_x(A, i, c - pos % V, pos % V, mx));
         const FF P = ff_mul(ev, inv);
-        const float2 Cp = cost_ff(A.cost, i, c, csh, csl);
+        const float2 Cp = cost_ff(cost, i, c, csh, csl);
         const FF C{Cp.x, Cp.y};
         const FF aP = ff_mul(ai, P);
         const FF F = ff_mul(aP, ff_at(A.v1, A.v1lo, c));

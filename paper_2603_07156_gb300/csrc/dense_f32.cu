@@ -1,5 +1,6 @@
 // Dense passes with float32 anchored matrix and float32 per-entry arithmetic
 // (mixed precision: float64 row/column totals).
+#define IBSN_FF_PASSES
 #include "dense_launch.cuh"
 
 namespace ibsn {

@@ -126,28 +126,39 @@ cudaError_t launch_dense_t(Pass p, DenseArgs<T>& A, int nsm, cudaStream_t st, Pa
 }
 
 
-// ---- float-float passes (float tile table) ----
-template <int TG, int CH>
-static const void* ff_kernel(Pass p) {
+// ---- float-float passes (float tile table; instantiated in one translation unit) ----
+#ifdef IBSN_FF_PASSES
+template <int TG, int CH, int KIND>
+static const void* ff_kernel_k(Pass p) {
   switch (p) {
-    case Pass::Plan: return (const void*)k_plan_ff<TG, CH>;
-    case Pass::Armijo: return (const void*)k_armijo_ff<TG, CH>;
-    case Pass::Certify: return (const void*)k_certify_ff<TG, CH>;
-    case Pass::Export: return (const void*)k_export_ff<TG, CH>;
-    case Pass::Reanchor: return (const void*)k_reanchor_ff<TG, CH>;
+    case Pass::Certify: return (const void*)k_certify_ff<TG, CH, KIND>;
+    case Pass::Reanchor: return (const void*)k_reanchor_ff<TG, CH, KIND>;
     default: return nullptr;
   }
 }
 
-static const void* ff_kernel_for(int q, Pass p) {
+template <int TG, int CH>
+static const void* ff_kernel(Pass p, int kind) {
+  switch (p) {
+    case Pass::Plan: return (const void*)k_plan_ff<TG, CH>;
+    case Pass::Armijo: return (const void*)k_armijo_ff<TG, CH>;
+    case Pass::Export: return (const void*)k_export_ff<TG, CH>;
+    default:
+      if (kind == 0) return ff_kernel_k<TG, CH, 0>(p);
+      if (kind == 1) return ff_kernel_k<TG, CH, 1>(p);
+      return ff_kernel_k<TG, CH, 2>(p);
+  }
+}
+
+static const void* ff_kernel_for(int q, Pass p, int kind) {
   using TT = TileTable<float>;
   switch (q) {
-    case 0: return ff_kernel<TT::tg[0], TT::ch[0]>(p);
-    case 1: return ff_kernel<TT::tg[1], TT::ch[1]>(p);
-    case 2: return ff_kernel<TT::tg[2], TT::ch[2]>(p);
-    case 3: return ff_kernel<TT::tg[3], TT::ch[3]>(p);
-    case 4: return ff_kernel<TT::tg[4], TT::ch[4]>(p);
-    case 5: return ff_kernel<TT::tg[5], TT::ch[5]>(p);
+    case 0: return ff_kernel<TT::tg[0], TT::ch[0]>(p, kind);
+    case 1: return ff_kernel<TT::tg[1], TT::ch[1]>(p, kind);
+    case 2: return ff_kernel<TT::tg[2], TT::ch[2]>(p, kind);
+    case 3: return ff_kernel<TT::tg[3], TT::ch[3]>(p, kind);
+    case 4: return ff_kernel<TT::tg[4], TT::ch[4]>(p, kind);
+    case 5: return ff_kernel<TT::tg[5], TT::ch[5]>(p, kind);
     default: return nullptr;
   }
 }
@@ -155,31 +166,32 @@ static const void* ff_kernel_for(int q, Pass p) {
 inline cudaError_t launch_dense_ff_t(Pass p, DenseArgs<float>& A, int nsm, cudaStream_t st, PassGeom* geom) {
   const int q = pick_tile<float>(A.n);
   if (q < 0) return cudaErrorInvalidValue;
-  const void* fn = ff_kernel_for(q, p);
+  const void* fn = ff_kernel_for(q, p, A.cost.kind);
   if (fn == nullptr) return cudaErrorInvalidValue;
   const int tg = TileTable<float>::tg[q];
   // row buffer of the row stream, then the float64 column accumulator
   const size_t smem = p == Pass::Reanchor ? 0
                       : (size_t)A.ldk * sizeof(float) + (p == Pass::Export ? 0 : (size_t)A.ldk * sizeof(double));
   static std::mutex mu;
-  static int occ_cache[TileTable<float>::count][(int)Pass::kCount] = {};
-  static size_t smem_set[TileTable<float>::count][(int)Pass::kCount] = {};
+  const int kk = (A.cost.kind >= 0 && A.cost.kind <= 2) ? A.cost.kind : 2;
+  static int occ_cache[TileTable<float>::count][(int)Pass::kCount][3] = {};
+  static size_t smem_set[TileTable<float>::count][(int)Pass::kCount][3] = {};
   int occ;
   {
     std::lock_guard<std::mutex> lk(mu);
     cudaError_t e;
-    if (smem > smem_set[q][(int)p]) {
+    if (smem > smem_set[q][(int)p][kk]) {
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      smem_set[q][(int)p] = smem;
-      occ_cache[q][(int)p] = 0;
+      smem_set[q][(int)p][kk] = smem;
+      occ_cache[q][(int)p][kk] = 0;
     }
-    occ = occ_cache[q][(int)p];
+    occ = occ_cache[q][(int)p][kk];
     if (occ == 0) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, tg, smem);
       if (e != cudaSuccess) return e;
       if (occ < 1) occ = 1;
-      occ_cache[q][(int)p] = occ;
+      occ_cache[q][(int)p][kk] = occ;
     }
   }
   int nb = nsm * occ;
@@ -201,5 +213,7 @@ inline cudaError_t launch_dense_ff_t(Pass p, DenseArgs<float>& A, int nsm, cudaS
   }
   return e;
 }
+
+#endif  // IBSN_FF_PASSES
 
 }  // namespace ibsn
