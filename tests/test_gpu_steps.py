@@ -99,7 +99,9 @@ def test_anchor_and_plan_pass(case):
         assert np.all((P[near] == 0.0) | (relnear <= tol * 60))
         big = kept
     rel = np.abs(P[big] - Pref[big]) / Pref[big]
-    assert rel.max() <= tol * 60, rel.max()
+    # float-float entries (float-float exp of a float64-accurate exponent):
+    # about 1e-14 relative; float64 passes: rounding of exp of exponents ~50
+    assert rel.max() <= (1e-12 if prec == "ff" else tol * 60), rel.max()
     assert np.abs(P - Pref).max() <= tol
     c, gn = ctx.plan()
     g_ref = O.gradient(Pref, prob.a, prob.b)
