@@ -356,12 +356,20 @@ struct Acc<float> {
     s = t;
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  // s += w x with the product fused into the compensated step
+  __device__ __forceinline__ void add_prod(float w, float x) {
+    const float y = fmaf(w, x, -c);
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
 };
 template <>
 struct Acc<double> {
   double s;
   __device__ __forceinline__ void zero() { s = 0.0; }
   __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_prod(double w, double x) { s = fma(w, x, s); }
   __device__ __forceinline__ double value() const { return s; }
 };
 

@@ -186,6 +186,14 @@ struct ColAcc {
       r[s][e].add(v);
     }
   }
+  __device__ __forceinline__ void add_prod(int s, int e, T w, T v) {
+    if constexpr (kSmem) {
+      const int64_t c = Tile<T, TG, CH>::col(s) + e;
+      if (c < ld) sm[c] = fma(w, v, sm[c]);
+    } else {
+      r[s][e].add_prod(w, v);
+    }
+  }
   // float64 partials (float64 passes) or float-float pairs {s, -c} (float
   // passes: no float64 conversion here; the column finish adds the pairs)
   __device__ __forceinline__ void flush(double* __restrict__ out, int64_t ldk) {
@@ -361,7 +369,7 @@ __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
 #pragma unroll
     for (int s = 0; s < CH; ++s)
 #pragma unroll
-      for (int e = 0; e < V; ++e) acc.add(s, e, w * t.x[s][e]);
+      for (int e = 0; e < V; ++e) acc.add_prod(s, e, w, t.x[s][e]);
   }
   acc.flush(A.colpart + (int64_t)blockIdx.x * A.ldk, A.ldk);
   if (threadIdx.x == 0) A.rowpart[blockIdx.x * kRowParts + 0] = (double)lpart;
@@ -432,7 +440,7 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
         for (int e = 0; e < V; ++e) em[e] = T(0);
       }
 #pragma unroll
-      for (int e = 0; e < V; ++e) acc.add(s, e, w * (t.x[s][e] + t.x[s][e] * em[e]));
+      for (int e = 0; e < V; ++e) acc.add_prod(s, e, w, fma(t.x[s][e], em[e], t.x[s][e]));
     }
   }
   acc.flush(A.colpart + (int64_t)blockIdx.x * A.ldk, A.ldk);
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
 // ---------------------------------------------------------------------------
 // Inexact stopping test (Eq. 8) with the rounding of Alg. 3.
 // v1 = omega_j = 1 - y_j, v2 = e_c,j, v3 = log e_c,j, v4 = (1-omega) log(1-omega)
-// + omega, s1 = S = ||e_c||_1.  e_r,i = a_i sum_j P_ij omega_j (z = 1: X = diag(a) P
+// + omega; S = ||e_c||_1 from scal[S_ECSUM].  e_r,i = a_i sum_j P_ij omega_j (z = 1: X = diag(a) P
 // has row sums a).  D_phi = sum_ij T_ij, T = Xhat log(Xhat/X) - Xhat + X >= 0 with
 // Xhat = X (1 - omega_j) + e_r,i e_c,j / S.  A column has omega_j > 0 or e_c,j > 0,
 // never both, so per entry (X = e^LX, extra = e_r,i e_c,j / S, L = log(extra/X)):
@@ -491,7 +499,8 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<T> rs;
   rs.start(A, dyn_sm, &s_mbar, r0, r1);
-  const T invS = (T)(A.s1 > 0.0 ? 1.0 / A.s1 : 0.0);
+  const double S_ec = A.scal[S_ECSUM];  // ||e_c||_1, formed on the device with the gradient
+  const T invS = (T)(S_ec > 0.0 ? 1.0 / S_ec : 0.0);
   T dpart = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {

@@ -171,7 +171,8 @@ struct ibsn_ctx {
   unsigned int* ctr = nullptr;
   int* err = nullptr;
   unsigned long long* pool_top = nullptr;
-  double* h_scal = nullptr;  // pinned copy of scal
+  double* h_scal = nullptr;  // pinned copy of scal (slots), then one int for the PCG error flag
+  int* h_perr = nullptr;
   int nbcap = 0;
 };
 
@@ -569,6 +570,16 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
   int perr = 0;
   // small float32 systems: one thread-block cluster (no grid-wide waits);
   // if its shared memory cannot hold the entries, the grid-wide kernel
+  // the direction's post-processing (copy, centring, slope) is queued right
+  // behind the solve; one read-back serves both
+  auto post = [&]() -> int {
+    CK(cudaMemcpyAsync(X->delta, X->pc.x, sizeof(double) * X->n, cudaMemcpyDeviceToDevice, X->st));
+    CK(launch_dir_post(X->n, X->eta, X->delta, X->g, X->scal, rb(X), X->st));
+    CK(cudaMemcpyAsync(X->h_perr, X->pc.err, sizeof(int), cudaMemcpyDeviceToHost, X->st));
+    RT(read_scal(X));
+    perr = *X->h_perr;
+    return IBSN_OK;
+  };
   bool done = false;
   if (!X->sp_f64 && X->nnz <= kClusterPcgMaxNnz && X->nnz < X->cl_fail_nnz) {
     bool launched = false;
@@ -578,10 +589,9 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
                             &launched));
     }
     if (launched) {
-      CK(cudaMemcpyAsync(&perr, X->pc.err, sizeof(int), cudaMemcpyDeviceToHost, X->st));
-      RT(read_scal(X));
+      RT(post());
       if (perr == kDevCapacity) {
-        X->cl_fail_nnz = X->nnz;
+        X->cl_fail_nnz = X->nnz;  // the entries did not fit: nothing was computed
       } else {
         done = true;
         X->cl_runs++;
@@ -594,13 +604,9 @@ int do_direction(ibsn_ctx* X, double shift, double rtol, int max_cg, int* iters,
       CK(launch_pcg(S, X->pc, X->m, X->n, X->istar, X->sp_f64, X->a, X->a32, X->eta, shift, rtol, max_cg,
                     X->prm.wait_timeout_s, X->nsm, X->nnz, X->scal, X->st));
     }
-    CK(cudaMemcpyAsync(&perr, X->pc.err, sizeof(int), cudaMemcpyDeviceToHost, X->st));
-    RT(read_scal(X));
+    RT(post());
   }
   if (perr == kDevTimeout) return IBSN_ERR_TIMEOUT;
-  CK(cudaMemcpyAsync(X->delta, X->pc.x, sizeof(double) * X->n, cudaMemcpyDeviceToDevice, X->st));
-  CK(launch_dir_post(X->n, X->eta, X->delta, X->g, X->scal, rb(X), X->st));
-  RT(read_scal(X));
   if (iters) *iters = (int)X->h_scal[S_CG_ITERS];
   if (resid) *resid = X->h_scal[S_CG_RES];
   if (prof0) {
@@ -655,7 +661,6 @@ int do_accept(ibsn_ctx* X, double t) {
 // a7: D_phi(Proj(X), X) (Eq. 8) at the current gamma (uses c, g of the current plan)
 int do_stop(ibsn_ctx* X, double* dphi) {
   CK(launch_round_prep(X->n, X->b, X->c, X->g, X->rv, X->gridrc, X->scal, rb(X), X->st));
-  RT(read_scal(X));
   PassGeom g;
   PassIn in;
   in.v1f = X->rv.om32;
@@ -666,7 +671,6 @@ int do_stop(ibsn_ctx* X, double* dphi) {
   in.v3d = X->rv.lec64;
   in.v4f = X->rv.hom32;
   in.v4d = X->rv.hom64;
-  in.s1 = X->h_scal[S_ECSUM];
   in.rowout = X->er;
   RT(run_pass(X, Pass::Stop, in, &g));
   // D_phi total: sum of row partials (no column work)
@@ -774,7 +778,8 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   X->st = st;
   X->nsm = nsm;
   X->prec = pp->precision == IBSN_PREC_MIXED ? 1 : 0;
-  cudaError_t e = cudaMallocHost(&X->h_scal, sizeof(double) * S_NSLOTS);
+  cudaError_t e = cudaMallocHost(&X->h_scal, sizeof(double) * (S_NSLOTS + 1));
+  if (e == cudaSuccess) X->h_perr = reinterpret_cast<int*>(X->h_scal + S_NSLOTS);
   if (e != cudaSuccess) {
     delete X;
     return set_cuda_error(e);
