@@ -150,6 +150,21 @@ int ibsn_workspace_size(const ibsn_problem* prob, const ibsn_params* params, siz
 int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* workspace,
                size_t workspace_bytes, ibsn_result* result, void* stream);
 
+/* Solve `count` independent problems (the batched workload: many uneven OT
+ * problems at once).  Problem q uses workspaces[q] (workspace_bytes[q] bytes,
+ * from ibsn_workspace_size for probs[q]) and fills results[q] (its status in
+ * results[q].status), exactly as ibsn_solve(&probs[q], params, ...) would:
+ * the results are identical to solving the problems one by one.  The solves
+ * run concurrently: `threads` host threads (<= 0: 8) take problems in index
+ * order, each issuing its problems' kernels on its own stream (streams[q]
+ * when `streams` is not null, otherwise a stream the thread creates and
+ * destroys), so passes of different problems overlap on the GPU.  Runs on the
+ * calling thread's current device.  Returns IBSN_OK when every problem
+ * converged, IBSN_NOT_CONVERGED when some did not, otherwise the first error
+ * in problem order (the other problems are still solved). */
+int ibsn_solve_batch(int count, const ibsn_problem* probs, const ibsn_params* params, void* const* workspaces,
+                     const size_t* workspace_bytes, ibsn_result* results, void* const* streams, int threads);
+
 /* ---------------------------------------------------------------------------
  * Step-level interface.  A context holds the state of one run of Alg. 2:
  * outer index k, cumulative potential Gamma^k (so that log X^k_ij equals

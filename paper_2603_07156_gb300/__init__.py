@@ -16,5 +16,6 @@ from .api import (  # noqa: F401
     alloc_workspace,
     params,
     solve,
+    solve_batch,
     workspace_size,
 )

@@ -60,6 +60,8 @@ _SIGS = {
     "ibsn_workspace_size": (C.c_int, [C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.POINTER(C.c_size_t)]),
     "ibsn_solve": (C.c_int, [C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.c_void_p, C.c_size_t,
                              C.POINTER(IbsnResult), C.c_void_p]),
+    "ibsn_solve_batch": (C.c_int, [C.c_int, C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_size_t), C.POINTER(IbsnResult), C.POINTER(C.c_void_p), C.c_int]),
     "ibsn_ctx_create": (C.c_int, [C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.c_void_p, C.c_size_t,
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "ibsn_ctx_destroy": (C.c_int, [C.c_void_p]),

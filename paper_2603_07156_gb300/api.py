@@ -129,6 +129,41 @@ def solve(problem: Problem, prm: N.IbsnParams | None = None, *, want_plan: bool 
     return out
 
 
+def solve_batch(problems: list, prm: N.IbsnParams | None = None, *, threads: int = 8,
+                workspaces: list | None = None) -> list[dict]:
+    """ibsn_solve_batch: independent problems solved concurrently (results as
+    from solve() one by one); returns one result dict per problem."""
+    lib = N.load()
+    prm = prm if prm is not None else params()
+    count = len(problems)
+    if count == 0:
+        return []
+    wss = workspaces if workspaces is not None else [alloc_workspace(p, prm) for p in problems]
+    probs = (N.IbsnProblem * count)(*[p.struct() for p in problems])
+    results = (N.IbsnResult * count)()
+    gammas, zetas = [], []
+    for q, p in enumerate(problems):
+        m, n = int(p.a.numel()), int(p.b.numel())
+        g = torch.empty(n, dtype=torch.float64, device=p.a.device)
+        z = torch.empty(m, dtype=torch.float64, device=p.a.device)
+        results[q].gamma, results[q].zeta, results[q].plan = _ptr(g), _ptr(z), None
+        gammas.append(g)
+        zetas.append(z)
+    ptrs = (C.c_void_p * count)(*[w.data_ptr() for w in wss])
+    sizes = (C.c_size_t * count)(*[w.numel() for w in wss])
+    torch.cuda.synchronize()  # inputs written on torch's streams are complete
+    code = lib.ibsn_solve_batch(count, probs, C.byref(prm), ptrs, sizes, results, None, int(threads))
+    N.check(code, "ibsn_solve_batch", allow=(0, 9))
+    out = []
+    for q in range(count):
+        r = results[q]
+        d = {f: getattr(r, f) for f, _ in N.IbsnResult._fields_
+             if f not in ("gamma", "zeta", "plan", "pass_ms", "pass_calls", "pass_bytes")}
+        d.update(gamma=gammas[q], zeta=zetas[q], converged=(r.status == 0))
+        out.append(d)
+    return out
+
+
 class Context:
     """Step-level access to one run of Alg. 2 (the hot-path rows one by one)."""
 

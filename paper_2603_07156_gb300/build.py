@@ -56,7 +56,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
         objs = list(ex.map(lambda u: _compile(u, extra), UNITS))
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [nvcc(), "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-lcudart"]
+        cmd = [nvcc(), "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-lcudart", "-lpthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

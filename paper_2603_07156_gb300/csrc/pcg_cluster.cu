@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -380,35 +382,38 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
   cl_sync();  // no CTA leaves while another may still write or read its shared memory
 }
 
-int g_cl_size = -1;  // cluster size this device schedules (0: none)
-
+// cluster size this device schedules (0: none), found once per process
 int cluster_size_for_device() {
-  if (g_cl_size >= 0) return g_cl_size;
-  g_cl_size = 0;
-  if (cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem) != cudaSuccess)
-    return 0;
-  if (cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    cudaGetLastError();
-  for (int csz : {kClMax, 8}) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)csz;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)csz);
-    cfg.blockDim = dim3(kClT);
-    cfg.dynamicSmemBytes = kClSmem;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_pcg_cluster, &cfg) == cudaSuccess && ncl >= 1) {
-      g_cl_size = csz;
-      break;
+  static std::once_flag once;
+  static int size = 0;
+  std::call_once(once, [] {
+    if (cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem) != cudaSuccess) {
+      cudaGetLastError();
+      return;
     }
-    cudaGetLastError();
-  }
-  return g_cl_size;
+    if (cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      cudaGetLastError();
+    for (int csz : {kClMax, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)csz;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)csz);
+      cfg.blockDim = dim3(kClT);
+      cfg.dynamicSmemBytes = kClSmem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_pcg_cluster, &cfg) == cudaSuccess && ncl >= 1) {
+        size = csz;
+        return;
+      }
+      cudaGetLastError();
+    }
+  });
+  return size;
 }
 
 }  // namespace

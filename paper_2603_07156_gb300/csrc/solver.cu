@@ -12,9 +12,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ibsn.h"
@@ -1039,6 +1041,44 @@ int ibsn_ctx_certify(ibsn_ctx* X, double* primal, double* dual, double* rel_gap,
   if (rel_gap) *rel_gap = c.gap;
   if (marg_viol) *marg_viol = c.viol;
   return IBSN_OK;
+}
+
+int ibsn_solve_batch(int count, const ibsn_problem* probs, const ibsn_params* params, void* const* workspaces,
+                     const size_t* workspace_bytes, ibsn_result* results, void* const* streams, int threads) {
+  if (count < 0) return IBSN_ERR_INVALID_ARG;
+  if (count == 0) return IBSN_OK;
+  if (!probs || !params || !workspaces || !workspace_bytes || !results) return IBSN_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IBSN_ERR_CUDA;
+  const int nt = std::max(1, std::min(threads > 0 ? threads : 8, count));
+  std::atomic<int> next{0};
+  std::vector<int> codes((size_t)count, IBSN_OK);
+  auto worker = [&]() {
+    if (cudaSetDevice(dev) != cudaSuccess) return;
+    cudaStream_t own = nullptr;
+    if (!streams && cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) own = nullptr;
+    for (;;) {
+      const int q = next.fetch_add(1);
+      if (q >= count) break;
+      void* st = streams ? streams[q] : (void*)own;
+      codes[(size_t)q] = ibsn_solve(&probs[q], params, workspaces[q], workspace_bytes[q], &results[q], st);
+    }
+    if (own) {
+      cudaStreamSynchronize(own);
+      cudaStreamDestroy(own);
+    }
+  };
+  std::vector<std::thread> pool;
+  pool.reserve((size_t)nt);
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (std::thread& t : pool) t.join();
+  int ret = IBSN_OK;
+  for (int q = 0; q < count; ++q) {
+    const int c = codes[(size_t)q];
+    if (c != IBSN_OK && c != IBSN_NOT_CONVERGED) return c;
+    if (c == IBSN_NOT_CONVERGED) ret = IBSN_NOT_CONVERGED;
+  }
+  return ret;
 }
 
 int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, size_t bytes, ibsn_result* res,

@@ -9,6 +9,9 @@
 // its rows in row order.
 #include <type_traits>
 
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -740,21 +743,17 @@ cudaError_t launch_csc_build(const SparseBufs& S, int m, int64_t n, int64_t ldk,
   k_scan_colptr<<<1, 1024, 0, st>>>(n, S.colptr);
   note_launch(4);
   const size_t smem = (size_t)n * sizeof(int32_t);
-  static bool attr_set[2] = {false, false};
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
   if (fp64) {
-    if (!attr_set[1]) {
-      cudaFuncSetAttribute(k_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set[1] = true;
-    }
     k_scatter<double><<<nb, 256, smem, st>>>(S.pool_col, (const double*)S.pool_val, S.row_start, S.row_len,
                                              S.blkpre, S.colptr, S.csc_row, (double*)S.csc_val, m, n, ldk, rpb);
     k_colstats<double><<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
         S.colptr, S.csc_row, (const double*)S.csc_val, (const double*)S.prow, a, istar, n, eta, S.crho, S.diag);
   } else {
-    if (!attr_set[0]) {
-      cudaFuncSetAttribute(k_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set[0] = true;
-    }
     k_scatter<float><<<nb, 256, smem, st>>>(S.pool_col, (const float*)S.pool_val, S.row_start, S.row_len,
                                             S.blkpre, S.colptr, S.csc_row, (float*)S.csc_val, m, n, ldk, rpb);
     k_colstats<float><<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
@@ -780,11 +779,13 @@ cudaError_t launch_export_sparse(const SparseBufs& S, int m, int64_t n, int ista
 
 template <int G, int E>
 static cudaError_t launch_pcg32_g(Pcg32Args& A, int nsm, cudaStream_t st) {
-  static int occ = 0;
+  static std::atomic<int> occ_cache{0};
+  int occ = occ_cache.load();
   if (occ == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32<G, E>, kPcgThreads, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+    occ_cache.store(occ);
   }
   // pcg_allreduce6 gives one thread of a block to each block's partial record
   if (nsm > kPcgThreads) return cudaErrorInvalidConfiguration;
@@ -795,11 +796,13 @@ static cudaError_t launch_pcg32_g(Pcg32Args& A, int nsm, cudaStream_t st) {
 
 template <typename T, int G, int E>
 static cudaError_t launch_pcg_g(PcgArgs<T>& A, int nsm, cudaStream_t st) {
-  static int occ = 0;
+  static std::atomic<int> occ_cache{0};
+  int occ = occ_cache.load();
   if (occ == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, G, E>, kPcgThreads, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+    occ_cache.store(occ);
   }
   // one block per SM keeps the barriers short; all blocks are co-resident
   const int nb = nsm;

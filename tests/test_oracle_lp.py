@@ -82,3 +82,18 @@ def test_separable_matches_highs():
     b = rng.uniform(0.1, 1, 5); b /= b.sum()
     C = u[:, None] + v[None, :]
     assert abs(lp.separable_optimum(u, v, a, b) - highs_optimum(C, a, b)) <= 1e-12
+
+
+def test_batched_points_are_the_batched_problems_draws():
+    """The bench's batched workload (points only, cost formed on the device)
+    draws exactly what workloads.batched_problems draws."""
+    import numpy as np
+    from workloads import batched_points, batched_problems
+    pts = batched_points(count=3, lo=30, hi=60)
+    full = batched_problems(count=3, lo=30, hi=60)
+    for (m, n, x, y, a, b, eta), p in zip(pts, full):
+        assert (m, n) == p.C.shape and eta == p.eta
+        assert np.array_equal(x, p.x) and np.array_equal(y, p.y)
+        assert np.array_equal(a, p.a) and np.array_equal(b, p.b)
+        C = ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)
+        assert np.allclose(C / C.max(), p.C, rtol=1e-15, atol=0)

@@ -11,6 +11,7 @@ from .generators import (  # noqa: F401
     gmm_points_problem,
     grid_problem,
     batched_problems,
+    batched_points,
     warmstart_gmm_problem,
     random_marginal,
     sq_euclidean_cost,

@@ -194,6 +194,23 @@ def batched_problems(count: int = 64, seed0: int = 100, lo: int = 500, hi: int =
     return out
 
 
+def batched_points(count: int = 64, seed0: int = 100, lo: int = 500, hi: int = 5000, eta: float = 1e-4):
+    """The draws of batched_problems without the cost matrices: per problem
+    (m, n, x, y, a, b, eta); the squared Euclidean cost divided by its max is
+    formed by the caller (on the device for the full-size batch)."""
+    out = []
+    for s in range(seed0, seed0 + count):
+        rng = np.random.default_rng(s)
+        m = int(rng.integers(lo, hi + 1))
+        n = int(rng.integers(lo, hi + 1))
+        x = rng.uniform(0.0, 1.0, size=(m, 2))
+        y = rng.uniform(0.0, 1.0, size=(n, 2))
+        a = random_marginal(rng, m)
+        b = random_marginal(rng, n)
+        out.append((m, n, x, y, a, b, eta))
+    return out
+
+
 def warmstart_gmm_problem(n: int, seed: int, k: int = 4, eta: float = 1e-4,
                           cost_dtype=np.float64) -> OTProblem:
     """2-D k-component Gaussian mixtures with Dirichlet(1) weights, means U[0,1]^2,
