@@ -32,6 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# the CPU oracle baseline runs on one host core: keep numpy's BLAS single-threaded
+# (set before numpy is first imported; the GPU path does not use it)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 METRIC = "s to rel. gap 1e-8 at m=n=16384; plan-pass HBM GB/s; speedup vs plain FP64"
 
 
@@ -198,6 +203,17 @@ def oracle_sample(a, b, scale, h, eta, rows):
     return dt * (n / rows)
 
 
+def grid_config(args, world: int) -> dict:
+    """The `config` of the grid workload's line (both arms)."""
+    h = args.grid
+    m = h * h
+    return {"workload": f"grid{h}x{h} smoothed random fields ({m} bins), eta={args.eta}, "
+                        f"C = squared grid distance / max rebuilt on the fly",
+            "m": m, "n": m, "eta": args.eta, "precision": args.precision, "gap_tol": 1e-8,
+            "l2": "inputs larger than L2 (anchored matrix 1 GiB f32 / 2 GiB f64), no flush",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, on a bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -205,7 +221,7 @@ def run_reference(args):
         return
     h = args.grid
     a, b, scale = grid_marginals(h)
-    passes = 1800  # dense passes of one GPU solve of this workload (eta 1e-4 .. 5e-5, measured order)
+    passes = 3400 if args.eta >= 1e-4 else 1800  # dense passes of one GPU solve of this workload (measured)
     for _ in range(max(args.warmup, 0)):
         oracle_sample(a, b, scale, h, args.eta, args.cpu_rows)
     vals = []
@@ -218,7 +234,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"grid{h}x{h} ({h * h} bins), eta={args.eta}", "m": h * h, "n": h * h},
+            "config": grid_config(args, 1),
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -421,11 +437,7 @@ def main():
         "metric": METRIC, "value": t_mean, "unit": "s", "n_gpus": rep["n_gpus"], "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mean * 1e3, "higher_is_better": False, "scaling": rep["scaling"],
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"grid{h}x{h} smoothed random fields ({m} bins), eta={args.eta}, "
-                               f"C = squared grid distance / max rebuilt on the fly",
-                   "m": m, "n": n, "eta": args.eta, "precision": args.precision, "gap_tol": 1e-8,
-                   "l2": "inputs larger than L2 (anchored matrix 1 GiB f32 / 2 GiB f64), no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": grid_config(args, world),
         "roofline": roof, "plan_pass": plan_pass, "fp64_plain": fp64,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "solve": {k: r0[k] for k in ("rel_gap", "primal", "dual", "outer_iters", "newton_iters", "cg_iters",
