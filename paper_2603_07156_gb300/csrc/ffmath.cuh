@@ -109,8 +109,10 @@ __device__ __forceinline__ FF ff_exp(FF x) {
   const float p2 = kf * L2;
   const float e2 = fmaf(kf, L2, -p2);
   FF r = ff_two_sum(t1, -p2);
-  r.lo += (x.lo - e2) - kf * L3;
-  r = ff_fast_two_sum(r.hi, r.lo);
+  // x.lo can be far above ulp(r.hi) once |x| is large: add it exactly too,
+  // so that every term left for the low word is below ulp(r.hi)
+  const FF s0 = ff_two_sum(r.hi, x.lo);
+  r = ff_fast_two_sum(s0.hi, s0.lo + ((r.lo - e2) - kf * L3));
   const FF r2 = ff_mul(r, r);
   const FF r3 = ff_mul(r2, r);
   const float rh = r.hi;
