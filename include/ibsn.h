@@ -260,6 +260,88 @@ int ibsn_ctx_certify(ibsn_ctx* ctx, double* primal, double* dual, double* rel_ga
 int ibsn_plan_pass_noalloc(const ibsn_problem* prob, int64_t k, const double* Gamma, const double* gamma,
                            double* colsum, double* grad_norm, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start.  The paper starts every solve from gamma^{0,0} = 0
+ * (Alg. 2).  These calls train and run a small network that predicts the
+ * optimal dual potential gamma (cost units, centred) of a point-cloud problem
+ * with squared-Euclidean cost, to be passed as params.gamma0; the zero start
+ * stays as the fallback and ibsn_judge_warm_start picks the start whose plan
+ * pass (Eqs. 6-7) has the smaller gradient norm.
+ *
+ * Network (three layers, width 128, bfloat16 weights, float32 arithmetic):
+ *   source point i: e_i = relu(W_s [x_i1, x_i2, m a_i] + b_s)
+ *   target point j: h_j = relu(W_t [y_j1, y_j2, n b_j] + b_t)
+ *   p_s = mean_i e_i, p_t = mean_j h_j
+ *   z_j = W_h [h_j; p_s; p_t] + b_h,  o_j = w_o . relu(z_j) + b_o
+ *   gamma_hat_j = o_j - mean_l o_l
+ * Parameters: one float32 vector of IBSN_WS_PARAM_COUNT values (the master
+ * copy that Adam updates), laid out row-major as W_s 128x3, b_s 128, W_t 128x3,
+ * b_t 128, W_h 128x384, b_h 128, w_o 128, b_o 1.  Every forward and backward
+ * pass rounds them to bfloat16 (nearest, ties to even) and computes with the
+ * rounded values; gradients are taken with respect to those rounded weights.
+ * Loss of a batch of Q problems: (1/Q) sum_q (1/n_q) ||gamma_hat_q - centred
+ * gamma*_q||^2.
+ * ------------------------------------------------------------------------- */
+#define IBSN_WS_HIDDEN 128
+#define IBSN_WS_PARAM_COUNT 50433
+#define IBSN_WS_MAX_POINTS 16384  /* per cloud and problem */
+
+/* A batch of point-cloud problems.  Problem q has m[q] source and n[q] target
+ * points (1 <= m[q], n[q] <= IBSN_WS_MAX_POINTS); its rows follow those of
+ * problems 0..q-1 in the concatenated device arrays. */
+typedef struct ibsn_ws_batch {
+  int32_t count;             /* Q >= 1 */
+  int32_t reserved_;
+  const int64_t* m;          /* host [Q] */
+  const int64_t* n;          /* host [Q] */
+  const double* x;           /* device, (sum m) x 2 row-major source coordinates */
+  const double* y;           /* device, (sum n) x 2 target coordinates */
+  const double* a;           /* device, sum m: source weights (each problem's sum 1) */
+  const double* b;           /* device, sum n: target weights */
+} ibsn_ws_batch;
+
+/* Adam hyper-parameters (Kingma & Ba 2015, Algorithm 1). */
+typedef struct ibsn_ws_adam {
+  double lr;                 /* default 1e-3 */
+  double beta1;              /* default 0.9 */
+  double beta2;              /* default 0.999 */
+  double eps;                /* default 1e-8 */
+} ibsn_ws_adam;
+
+/* Number of parameters (IBSN_WS_PARAM_COUNT). */
+int64_t ibsn_ws_param_count(void);
+/* Fill *hp with the defaults above.  Never fails. */
+void ibsn_ws_adam_default(ibsn_ws_adam* hp);
+
+/* Bytes of device workspace (256-byte aligned) for a batch of these sizes. */
+int ibsn_ws_workspace_size(const ibsn_ws_batch* batch, size_t* bytes);
+
+/* Forward pass: gamma_hat (device, sum n float64, centred per problem). */
+int ibsn_ws_predict(const ibsn_ws_batch* batch, const float* params, double* gamma_hat, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Forward and backward pass against targets gamma_star (device, sum n; each
+ * problem's target is centred inside): the batch loss (host, nullable; the
+ * call then synchronises the stream) and its gradient grad (device float32,
+ * IBSN_WS_PARAM_COUNT, overwritten).  gamma_hat (device, nullable) receives
+ * the prediction.  Reductions run in a fixed order: the result does not
+ * depend on the launch or on timing. */
+int ibsn_ws_loss_grad(const ibsn_ws_batch* batch, const float* params, const double* gamma_star, double* loss,
+                      float* grad, double* gamma_hat, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One Adam step t >= 1 on `count` float32 parameters (device arrays params,
+ * first and second moments m1, m2, updated in place; gradient grad). */
+int ibsn_ws_adam_step(int64_t count, float* params, float* m1, float* m2, const float* grad, int64_t t,
+                      const ibsn_ws_adam* hp, void* stream);
+
+/* Judge a warm start for one problem: plan passes (Eqs. 6-7) at k = 0 in the
+ * working precision of `params` from gamma_hat (device n) and from zero;
+ * reports both gradient norms (host, nullable) and *use_warm = 1 when the
+ * warm start's is smaller.  Uses the solver workspace of ibsn_workspace_size. */
+int ibsn_judge_warm_start(const ibsn_problem* prob, const ibsn_params* params, const double* gamma_hat,
+                          void* workspace, size_t workspace_bytes, double* grad_norm_warm,
+                          double* grad_norm_zero, int32_t* use_warm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,8 @@ from .generators import (  # noqa: F401
     batched_problems,
     batched_points,
     warmstart_gmm_problem,
+    warmstart_init_params,
+    WARMSTART_SHAPES,
     random_marginal,
     sq_euclidean_cost,
     grid_sq_cost,

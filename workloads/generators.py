@@ -16,7 +16,9 @@ Workload recipes (the five standard configurations):
           the DOTmark / MNIST image pairs, which are not used here.
 * ``c3``  64 problems, seeds 100..163, m, n ~ U{500..5000} independently,
           2-D uniform points, squared Euclidean / max, eta = 1e-4.
-* ``c4``  2-D 4-component Gaussian mixtures with random weights (warm start).
+* ``c4``  2-D 4-component Gaussian mixtures with random weights (warm start):
+          ``warmstart_gmm_problem``; network initial weights from
+          ``warmstart_init_params``.
 """
 
 from __future__ import annotations
@@ -234,6 +236,27 @@ def warmstart_gmm_problem(n: int, seed: int, k: int = 4, eta: float = 1e-4,
     C, scale = _normalised_by_max(sq_euclidean_cost(x, y))
     return OTProblem(C=C.astype(cost_dtype), a=a, b=b, eta=eta, name=f"ws_gmm_{n}_s{seed}",
                      x=x, y=y, cost_scale=scale)
+
+
+# Shapes of the warm-start network's parameters, in the order of its flat
+# float32 vector (W_s, b_s, W_t, b_t, W_h, b_h, w_o, b_o; row-major).
+WARMSTART_SHAPES = [(128, 3), (128,), (128, 3), (128,), (128, 384), (128,), (128,), (1,)]
+
+
+def warmstart_init_params(seed: int) -> np.ndarray:
+    """Initial float32 parameters of the warm-start network: weights drawn
+    U(-sqrt(6/fan_in), +sqrt(6/fan_in)) (fan_in = the row length; 128 for
+    w_o), biases 0.  Draw order: the weight tensors in layout order."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k, shape in enumerate(WARMSTART_SHAPES):
+        if k in (1, 3, 5, 7):
+            parts.append(np.zeros(shape))
+        else:
+            fan_in = shape[-1]
+            lim = np.sqrt(6.0 / fan_in)
+            parts.append(rng.uniform(-lim, lim, size=shape))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
 def workload(name: str, cost_dtype=np.float64) -> OTProblem:
