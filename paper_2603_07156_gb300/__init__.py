@@ -19,3 +19,4 @@ from .api import (  # noqa: F401
     solve_batch,
     workspace_size,
 )
+from . import warmstart  # noqa: F401,E402

@@ -50,6 +50,18 @@ class IbsnResult(C.Structure):
         ("pass_ms", C.c_double * 16), ("pass_calls", C.c_int64 * 16), ("pass_bytes", C.c_double * 16),
     ]
 
+class IbsnWsBatch(C.Structure):
+    _fields_ = [
+        ("count", C.c_int32), ("reserved_", C.c_int32),
+        ("m", C.POINTER(C.c_int64)), ("n", C.POINTER(C.c_int64)),
+        ("x", C.c_void_p), ("y", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p),
+    ]
+
+
+class IbsnWsAdam(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double)]
+
+
 PASS_KINDS = ["plan", "armijo", "stop", "sparsify", "certify", "anchor", "pcg", "vector"]
 
 
@@ -62,6 +74,17 @@ _SIGS = {
                              C.POINTER(IbsnResult), C.c_void_p]),
     "ibsn_solve_batch": (C.c_int, [C.c_int, C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_size_t), C.POINTER(IbsnResult), C.POINTER(C.c_void_p), C.c_int]),
+    "ibsn_ws_param_count": (C.c_int64, []),
+    "ibsn_ws_adam_default": (None, [C.POINTER(IbsnWsAdam)]),
+    "ibsn_ws_workspace_size": (C.c_int, [C.POINTER(IbsnWsBatch), C.POINTER(C.c_size_t)]),
+    "ibsn_ws_predict": (C.c_int, [C.POINTER(IbsnWsBatch), C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
+    "ibsn_ws_loss_grad": (C.c_int, [C.POINTER(IbsnWsBatch), C.c_void_p, C.c_void_p, c_double_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "ibsn_ws_adam_step": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                    C.POINTER(IbsnWsAdam), C.c_void_p]),
+    "ibsn_judge_warm_start": (C.c_int, [C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.c_void_p, C.c_void_p,
+                                        C.c_size_t, c_double_p, c_double_p, C.POINTER(C.c_int32), C.c_void_p]),
     "ibsn_ctx_create": (C.c_int, [C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.c_void_p, C.c_size_t,
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "ibsn_ctx_destroy": (C.c_int, [C.c_void_p]),

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibsn_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["dense_f32.cu", "dense_f64.cu", "vec.cu", "sparse.cu", "pcg_cluster.cu", "solver.cu", "noalloc.cu"]
+UNITS = ["dense_f32.cu", "dense_f64.cu", "vec.cu", "sparse.cu", "pcg_cluster.cu", "solver.cu", "noalloc.cu",
+         "warmstart.cu"]
 
 
 def nvcc() -> str:

@@ -1250,4 +1250,29 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
   return status;
 }
 
+// Warm start or zero start: one plan pass (Eqs. 6-7) at k = 0 from each, in
+// the precision the solve starts in; the smaller gradient norm wins (a
+// non-finite norm never wins).
+int ibsn_judge_warm_start(const ibsn_problem* prob, const ibsn_params* params, const double* gamma_hat,
+                          void* workspace, size_t workspace_bytes, double* grad_norm_warm, double* grad_norm_zero,
+                          int32_t* use_warm, void* stream) {
+  if (!prob || !params || !gamma_hat || !use_warm) return IBSN_ERR_INVALID_ARG;
+  ibsn_ctx* X = nullptr;
+  RT(ctx_create_impl(prob, params, workspace, workspace_bytes, (cudaStream_t)stream, &X));
+  struct Guard {
+    ibsn_ctx* X;
+    ~Guard() { ibsn_ctx_destroy(X); }
+  } guard{X};
+  const int prec = X->prec;
+  double gw = 0.0, gz = 0.0;
+  RT(ibsn_ctx_set_state(X, 0, nullptr, gamma_hat, prec));
+  RT(ibsn_ctx_plan(X, nullptr, &gw));
+  RT(ibsn_ctx_set_state(X, 0, nullptr, nullptr, prec));
+  RT(ibsn_ctx_plan(X, nullptr, &gz));
+  if (grad_norm_warm) *grad_norm_warm = gw;
+  if (grad_norm_zero) *grad_norm_zero = gz;
+  *use_warm = (std::isfinite(gw) && gw < gz) ? 1 : 0;
+  return IBSN_OK;
+}
+
 }  // extern "C"

@@ -44,6 +44,10 @@ int main(void) {
   F(ibsn_params, gamma0); F(ibsn_params, nnz_cap); F(ibsn_params, max_outer); F(ibsn_params, profile);
   F(ibsn_result, primal); F(ibsn_result, outer_iters); F(ibsn_result, status); F(ibsn_result, dense_passes);
   F(ibsn_result, kernel_launches); F(ibsn_result, pass_ms); F(ibsn_result, pass_calls); F(ibsn_result, pass_bytes);
+  printf("sizeof ibsn_ws_batch %zu\n", sizeof(ibsn_ws_batch));
+  printf("sizeof ibsn_ws_adam %zu\n", sizeof(ibsn_ws_adam));
+  F(ibsn_ws_batch, m); F(ibsn_ws_batch, n); F(ibsn_ws_batch, x); F(ibsn_ws_batch, b);
+  F(ibsn_ws_adam, lr); F(ibsn_ws_adam, eps);
   return 0;
 }
 """
@@ -62,7 +66,10 @@ int main(void) {
     assert got[("sizeof", "ibsn_problem")] == ctypes.sizeof(N.IbsnProblem)
     assert got[("sizeof", "ibsn_params")] == ctypes.sizeof(N.IbsnParams)
     assert got[("sizeof", "ibsn_result")] == ctypes.sizeof(N.IbsnResult)
-    structs = {"ibsn_problem": N.IbsnProblem, "ibsn_params": N.IbsnParams, "ibsn_result": N.IbsnResult}
+    assert got[("sizeof", "ibsn_ws_batch")] == ctypes.sizeof(N.IbsnWsBatch)
+    assert got[("sizeof", "ibsn_ws_adam")] == ctypes.sizeof(N.IbsnWsAdam)
+    structs = {"ibsn_problem": N.IbsnProblem, "ibsn_params": N.IbsnParams, "ibsn_result": N.IbsnResult,
+               "ibsn_ws_batch": N.IbsnWsBatch, "ibsn_ws_adam": N.IbsnWsAdam}
     for (s, f), off in got.items():
         if s in structs:
             assert getattr(structs[s], f).offset == off, (s, f)
@@ -100,3 +107,38 @@ def test_workspace_size_rejects_bad_problems(lib):
     assert lib.ibsn_workspace_size(ctypes.byref(pr), ctypes.byref(pm), ctypes.byref(out)) == 8  # unsupported
     pr.n, pr.ldc = 4, 2
     assert lib.ibsn_workspace_size(ctypes.byref(pr), ctypes.byref(pm), ctypes.byref(out)) == 1  # ldc < n
+
+
+def test_warm_start_host_checks(lib):
+    """Parameter count, Adam defaults and argument checks of the warm-start
+    calls (paths that return before any device work)."""
+    from paper_2603_07156_gb300 import _native as N
+    assert lib.ibsn_ws_param_count() == 50433
+    hp = N.IbsnWsAdam()
+    lib.ibsn_ws_adam_default(ctypes.byref(hp))
+    assert (hp.lr, hp.beta1, hp.beta2, hp.eps) == (1e-3, 0.9, 0.999, 1e-8)
+    out = ctypes.c_size_t()
+    b = N.IbsnWsBatch()
+    b.count = 0
+    assert lib.ibsn_ws_workspace_size(ctypes.byref(b), ctypes.byref(out)) == 1
+    ms = (ctypes.c_int64 * 2)(5, 300)
+    ns = (ctypes.c_int64 * 2)(7, 1)
+    b.count, b.m, b.n = 2, ms, ns
+    assert lib.ibsn_ws_workspace_size(ctypes.byref(b), ctypes.byref(out)) == 0
+    small = out.value
+    assert small >= 4 * 128 * (305 * 2 + 8 * 4) and small % 256 == 0
+    ms[1] = 3000
+    assert lib.ibsn_ws_workspace_size(ctypes.byref(b), ctypes.byref(out)) == 0 and out.value > small
+    ms[1] = 16385
+    assert lib.ibsn_ws_workspace_size(ctypes.byref(b), ctypes.byref(out)) == 8      # above the point limit
+    ms[1] = 0
+    assert lib.ibsn_ws_workspace_size(ctypes.byref(b), ctypes.byref(out)) == 1      # empty cloud
+    ms[1] = 300
+    # null device pointers, then a misaligned workspace: rejected before any device work
+    assert lib.ibsn_ws_predict(ctypes.byref(b), 256, 256, 256, 1 << 30, None) == 1
+    b.x = b.y = b.a = b.b = 256
+    assert lib.ibsn_ws_predict(ctypes.byref(b), 256, 256, 300, 1 << 30, None) == 4
+    assert lib.ibsn_ws_predict(ctypes.byref(b), 256, 256, 512, 16, None) == 4       # too small
+    assert lib.ibsn_ws_adam_step(10, 256, 256, 256, 256, 0, ctypes.byref(hp), None) == 1  # t = 0
+    hp.beta1 = 1.0
+    assert lib.ibsn_ws_adam_step(10, 256, 256, 256, 256, 1, ctypes.byref(hp), None) == 1

@@ -1,0 +1,220 @@
+"""Learned warm start on the GPU: forward pass, gradient and Adam step of the
+network's kernels against the float64 oracle (oracle/warmstart.py), then
+training on solves the method generates and what the trained network gains.
+
+Tolerances.  The kernels compute in float32 with the same bfloat16-rounded
+weights as the oracle.  Dot products have at most 384 terms of size O(1), so
+their float32 error is below 1e-5 of the output scale; the tests allow 5e-5
+for predictions and 2e-4 of each parameter block's largest gradient (the
+weight gradients sum a few hundred rows per partial before a sum over
+partials).  Adam is elementwise float32: 1e-6 relative.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import warmstart as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2603_07156_gb300 as pkg
+    return pkg
+
+
+def _clouds(sizes, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for m, n in sizes:
+        x = rng.uniform(0, 1, (m, 2))
+        y = rng.uniform(0, 1, (n, 2))
+        a = rng.uniform(0.1, 1, m)
+        b = rng.uniform(0.1, 1, n)
+        out.append((x, a / a.sum(), y, b / b.sum()))
+    return out
+
+
+def _theta(seed):
+    """Initial weights plus random biases (so that no unit starts at a kink)."""
+    t = W.warmstart_init_params(seed)
+    P = O.unflatten(t)
+    rng = np.random.default_rng(seed + 1000)
+    for name in ("b_s", "b_t", "b_h"):
+        P[name][:] = rng.normal(0, 0.2, P[name].shape)
+    P["b_o"][:] = 0.25
+    return t
+
+
+def _batch(G, probs):
+    return G.warmstart.PointBatch([p[0] for p in probs], [p[2] for p in probs], [p[1] for p in probs],
+                                  [p[3] for p in probs])
+
+
+def _min_abs_preactivation(theta, probs):
+    P = O.unflatten(O.bf16_round(theta))
+    lo = np.inf
+    for x, a, y, b in probs:
+        F = O.forward(P, x, a, y, b)
+        lo = min(lo, np.abs(F["pre_s"]).min(), np.abs(F["pre_t"]).min(), np.abs(F["z"]).min())
+    return lo
+
+
+# ragged: single points, tails shorter than a tile, several 16- and 64-point tiles
+SIZES = [(1, 1), (5, 3), (37, 70), (130, 129), (64, 17), (200, 16)]
+
+
+def test_predict_matches_oracle(G):
+    probs = _clouds(SIZES, 0)
+    theta = _theta(1)
+    batch = _batch(G, probs)
+    gh = G.warmstart.predict(batch, torch.tensor(theta, device="cuda")).cpu().numpy()
+    parts = np.split(gh, np.cumsum([n for _, n in SIZES])[:-1])
+    for (x, a, y, b), got in zip(probs, parts):
+        want = O.predict(theta, x, a, y, b)
+        scale = max(1.0, np.abs(want).max())
+        assert np.abs(got - want).max() <= 5e-5 * scale, (len(b), np.abs(got - want).max())
+    assert parts[0][0] == 0.0  # one target point: the centred prediction is exactly 0
+
+
+def test_loss_and_gradient_match_oracle(G):
+    sizes = [(70, 150), (33, 16), (1, 5), (129, 64)]
+    probs = _clouds(sizes, 2)
+    theta = _theta(3)
+    # inputs chosen away from relu kinks, where float32 and float64 could take
+    # different branches
+    assert _min_abs_preactivation(theta, probs) > 1e-5
+    rng = np.random.default_rng(4)
+    gstar = [rng.normal(0, 0.1, n) for _, n in sizes]
+    want_loss, want_g = O.loss_and_grad(theta, [(x, a, y, b) for x, a, y, b in probs], gstar)
+    batch = _batch(G, probs)
+    gs = torch.tensor(np.concatenate(gstar), dtype=torch.float64, device="cuda")
+    loss, g, gh = G.warmstart.loss_grad(batch, torch.tensor(theta, device="cuda"), gs)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - want_loss) <= 1e-5 * want_loss
+    gmax = np.abs(want_g).max()
+    off = 0
+    for name, shape in O.SHAPES:
+        size = int(np.prod(shape))
+        w, got = want_g[off:off + size], g[off:off + size]
+        tol = 2e-4 * max(np.abs(w).max(), 1e-3 * gmax)
+        assert np.abs(got - w).max() <= tol, (name, np.abs(got - w).max(), tol)
+        off += size
+    # the same call returns the prediction
+    parts = np.split(gh.cpu().numpy(), np.cumsum([n for _, n in sizes])[:-1])
+    for (x, a, y, b), got in zip(probs, parts):
+        assert np.abs(got - O.predict(theta, x, a, y, b)).max() <= 5e-5
+
+
+def test_gradient_is_deterministic(G):
+    probs = _clouds([(300, 257), (90, 400)], 5)
+    theta = torch.tensor(_theta(6), device="cuda")
+    batch = _batch(G, probs)
+    gs = torch.randn(657, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    l1, g1, _ = G.warmstart.loss_grad(batch, theta, gs)
+    l2, g2, _ = G.warmstart.loss_grad(batch, theta, gs)
+    assert l1 == l2 and torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("t", [1, 7])
+def test_adam_step_matches_oracle(G, t):
+    rng = np.random.default_rng(t)
+    n = O.PARAM_COUNT
+    p = rng.normal(0, 1, n).astype(np.float32)
+    m1 = (rng.normal(0, 1, n) * (t > 1)).astype(np.float32)
+    m2 = (rng.uniform(0.5, 2, n) * (t > 1)).astype(np.float32)
+    g = rng.normal(0, 1, n).astype(np.float32)
+    want_p, want_m1, want_m2 = O.adam_step(p.astype(np.float64), m1.astype(np.float64), m2.astype(np.float64),
+                                           g.astype(np.float64), t, 1e-3, 0.9, 0.999, 1e-8)
+    P, M1, M2, Gd = (torch.tensor(v, device="cuda") for v in (p, m1, m2, g))
+    G.warmstart.adam_step(P, M1, M2, Gd, t, G.warmstart.adam_hparams())
+    assert np.allclose(M1.cpu().numpy(), want_m1, rtol=1e-6, atol=1e-7)
+    assert np.allclose(M2.cpu().numpy(), want_m2, rtol=1e-6, atol=1e-7)
+    assert np.allclose(P.cpu().numpy(), want_p, rtol=1e-6, atol=1e-8)
+
+
+def test_bad_arguments_raise(G):
+    with pytest.raises(ValueError):
+        G.warmstart.predict(_batch(G, _clouds([(3, 3)], 0)), torch.zeros(10, device="cuda"))
+    with pytest.raises(G._native.IbsnError):
+        G.warmstart.PointBatch([np.zeros((16385, 2))], [np.zeros((2, 2))], [np.ones(16385) / 16385],
+                               [np.ones(2) / 2]).workspace()
+
+
+# ---------------------------------------------------------------------------
+# training on solves of the method, and the gain
+# ---------------------------------------------------------------------------
+
+N_TRAIN, N_HELD, NPTS = 64, 8, 128
+
+
+def _gpu_problem(G, p):
+    t = lambda v: torch.tensor(v, dtype=torch.float64, device="cuda")  # noqa: E731
+    return G.Problem(a=t(p.a), b=t(p.b), eta=p.eta, C=t(p.C))
+
+
+@pytest.fixture(scope="module")
+def trained(G):
+    """Solve 64 training and 8 held-out problems (2-D 4-component Gaussian
+    mixtures, m = n = 128, eta = 1e-4), then train the network for 600 Adam
+    steps on minibatches of 16 training problems."""
+    prm = G.params(precision="mixed")
+    probs = [W.warmstart_gmm_problem(NPTS, 5000 + s) for s in range(N_TRAIN + N_HELD)]
+    plain = []
+    for p in probs:
+        r = G.solve(_gpu_problem(G, p), prm)
+        assert r["converged"], r["rel_gap"]
+        plain.append(r)
+    train, held = probs[:N_TRAIN], probs[N_TRAIN:]
+    batches = []
+    for k in range(0, N_TRAIN, 16):
+        chunk = list(range(k, k + 16))
+        b = G.warmstart.PointBatch.from_problems([train[i] for i in chunk])
+        gs = torch.cat([plain[i]["gamma"] for i in chunk]).contiguous()
+        batches.append((b, gs))
+    tr = G.warmstart.Trainer(W.warmstart_init_params(0))
+    losses = [tr.step(*batches[s % len(batches)]) for s in range(600)]
+    return dict(prm=prm, probs=probs, plain=plain, held=held, theta=tr.theta, losses=losses)
+
+
+def test_training_reduces_loss_and_generalises(G, trained):
+    losses = trained["losses"]
+    assert np.mean(losses[-8:]) < 0.3 * np.mean(losses[:4]), (losses[:4], losses[-8:])
+    hb = G.warmstart.PointBatch.from_problems(trained["held"])
+    gh = hb.split(G.warmstart.predict(hb, trained["theta"]))
+    mse_net = mse_zero = 0.0
+    for q in range(N_HELD):
+        gs = trained["plain"][N_TRAIN + q]["gamma"]
+        gs = gs - gs.mean()
+        mse_net += float(((gh[q] - gs) ** 2).mean())
+        mse_zero += float((gs ** 2).mean())
+    assert mse_net < 0.5 * mse_zero, (mse_net, mse_zero)
+
+
+def test_warm_start_gain_over_zero_start(G, trained):
+    """Held-out problems solved from the judged warm start and from zero: the
+    same certified optimum, and fewer Sinkhorn warm-up iterations in total."""
+    hb = G.warmstart.PointBatch.from_problems(trained["held"])
+    gh = hb.split(G.warmstart.predict(hb, trained["theta"]))
+    prm = trained["prm"]
+    rows = []
+    for q, p in enumerate(trained["held"]):
+        plain = trained["plain"][N_TRAIN + q]
+        warm = G.warmstart.solve_warm(_gpu_problem(G, p), prm, gh[q].contiguous())
+        assert warm["converged"] and warm["rel_gap"] <= 1e-8
+        assert abs(warm["primal"] - plain["primal"]) <= 1e-7 * abs(plain["primal"])
+        assert min(warm["grad_norm_warm"], warm["grad_norm_zero"]) <= warm["grad_norm_zero"]
+        rows.append((warm["warm_used"], plain["sinkhorn_iters"], warm["sinkhorn_iters"], plain["outer_iters"],
+                     warm["outer_iters"], plain["seconds"], warm["seconds"]))
+    used = sum(r[0] for r in rows)
+    sk_plain, sk_warm = sum(r[1] for r in rows), sum(r[2] for r in rows)
+    print(f"\nwarm start on {N_HELD} held-out problems: used {used}, Sinkhorn iterations {sk_plain} -> {sk_warm}, "
+          f"outer {sum(r[3] for r in rows)} -> {sum(r[4] for r in rows)}, "
+          f"seconds {sum(r[5] for r in rows):.3f} -> {sum(r[6] for r in rows):.3f}")
+    assert used >= 1
+    assert sk_warm <= sk_plain
