@@ -415,14 +415,16 @@ __global__ void k_ws_wgrad_finish(int splits, int R, int CX, int ones, const flo
   else grad[offB + r] = s;
 }
 
-// Adam (Kingma & Ba 2015, Algorithm 1); bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
+// Adam (Kingma & Ba 2015, Algorithm 1); omb1 = 1 - beta1, omb2 = 1 - beta2,
+// bc1 = 1 - beta1^t, bc2 = 1 - beta2^t, each formed in float64 on the host
+// (1 - beta2 formed in float32 from beta2 = 0.999 would be off by 1e-5).
 __global__ void k_ws_adam(int64_t count, float* __restrict__ p, float* __restrict__ m1, float* __restrict__ m2,
-                          const float* __restrict__ g, float lr, float b1, float b2, float eps, float bc1,
-                          float bc2) {
+                          const float* __restrict__ g, float lr, float b1, float b2, float omb1, float omb2,
+                          float eps, float bc1, float bc2) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
-    const float a = fmaf(b1, m1[i], (1.f - b1) * gi);
-    const float v = fmaf(b2, m2[i], (1.f - b2) * gi * gi);
+    const float a = fmaf(b1, m1[i], omb1 * gi);
+    const float v = fmaf(b2, m2[i], omb2 * gi * gi);
     m1[i] = a;
     m2[i] = v;
     p[i] -= lr * (a / bc1) / (sqrtf(v / bc2) + eps);
@@ -652,9 +654,9 @@ extern "C" int ibsn_ws_adam_step(int64_t count, float* params, float* m1, float*
   const double bc1 = 1.0 - std::pow(hp->beta1, (double)t);
   const double bc2 = 1.0 - std::pow(hp->beta2, (double)t);
   const int64_t blocks = (count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096;
-  k_ws_adam<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(count, params, m1, m2, grad, (float)hp->lr,
-                                                                (float)hp->beta1, (float)hp->beta2, (float)hp->eps,
-                                                                (float)bc1, (float)bc2);
+  k_ws_adam<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+      count, params, m1, m2, grad, (float)hp->lr, (float)hp->beta1, (float)hp->beta2, (float)(1.0 - hp->beta1),
+      (float)(1.0 - hp->beta2), (float)hp->eps, (float)bc1, (float)bc2);
   ibsn::note_launch();
   return launched();
 }
