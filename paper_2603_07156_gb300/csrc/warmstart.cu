@@ -544,7 +544,7 @@ int run_forward(const ibsn_ws_batch* B, const WsGeom& g, const WsBufs& w, const 
   const int htiles = (int)((g.maxn + kHeadTile - 1) / kHeadTile);
   k_ws_head_fwd<<<dim3(htiles, g.Q), kH, 0, st>>>(w.toff, w.pre_t, w.ctx, w.wb, w.z, w.out);
   k_ws_center<<<g.Q, kCenterThreads, 0, st>>>(w.toff, w.out, g.Q, gstar, gamma_hat, w.lossq, w.dout);
-  ibsn::note_launch(11);
+  ibsn::note_launch(10);
   return launched();
 }
 
