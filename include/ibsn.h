@@ -265,8 +265,8 @@ int ibsn_plan_pass_noalloc(const ibsn_problem* prob, int64_t k, const double* Ga
  * (Alg. 2).  These calls train and run a small network that predicts the
  * optimal dual potential gamma (cost units, centred) of a point-cloud problem
  * with squared-Euclidean cost, to be passed as params.gamma0; the zero start
- * stays as the fallback and ibsn_judge_warm_start picks the start whose plan
- * pass (Eqs. 6-7) has the smaller gradient norm.
+ * stays as the fallback and ibsn_judge_warm_start picks the start with the
+ * smaller semi-dual objective (Eq. 5).
  *
  * Network (three layers, width 128, bfloat16 weights, float32 arithmetic):
  *   source point i: e_i = relu(W_s [x_i1, x_i2, m a_i] + b_s)
@@ -334,13 +334,18 @@ int ibsn_ws_loss_grad(const ibsn_ws_batch* batch, const float* params, const dou
 int ibsn_ws_adam_step(int64_t count, float* params, float* m1, float* m2, const float* grad, int64_t t,
                       const ibsn_ws_adam* hp, void* stream);
 
-/* Judge a warm start for one problem: plan passes (Eqs. 6-7) at k = 0 in the
- * working precision of `params` from gamma_hat (device n) and from zero;
- * reports both gradient norms (host, nullable) and *use_warm = 1 when the
- * warm start's is smaller.  Uses the solver workspace of ibsn_workspace_size. */
+/* Judge a warm start for one problem (Alg. 2 starts from gamma = 0): the
+ * semi-dual objective of Eq. 5 at k = 0 (X^0 = a b^T),
+ *   L^0(gamma) = -b^T gamma + eta sum_i a_i log sum_j a_i b_j exp((gamma_j - C_ij)/eta),
+ * evaluated in float64 at gamma_hat (device n) and at 0 (host outs,
+ * nullable); *use_warm = 1 when the warm start's value is finite and smaller.
+ * Also reports the gradient norms of Eq. 7 from both starts (plan passes in
+ * the working precision of `params`; host outs, nullable).  Uses the solver
+ * workspace of ibsn_workspace_size. */
 int ibsn_judge_warm_start(const ibsn_problem* prob, const ibsn_params* params, const double* gamma_hat,
-                          void* workspace, size_t workspace_bytes, double* grad_norm_warm,
-                          double* grad_norm_zero, int32_t* use_warm, void* stream);
+                          void* workspace, size_t workspace_bytes, double* objective_warm,
+                          double* objective_zero, double* grad_norm_warm, double* grad_norm_zero,
+                          int32_t* use_warm, void* stream);
 
 #ifdef __cplusplus
 }

@@ -188,4 +188,11 @@ cudaError_t launch_pcg(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, 
 int pcg_max_blocks(int nsm);
 cudaError_t launch_len_stats(const SparseBufs& S, int m, int64_t n, double* scal, cudaStream_t st);
 
+// Semi-dual objective at k = 0 (Eq. 5 with X^0 = a b^T):
+//   L^0(gamma) = -b^T gamma + eta sum_i a_i log sum_j a_i b_j exp((gamma_j - C_ij)/eta),
+// float64 throughout; gamma nullable (zero).  rowval: m doubles of scratch;
+// the value is written to *out (device).
+cudaError_t launch_semidual0(const CostRef& cost, int m, int64_t n, double eta, const double* a, const double* b,
+                             const double* logb, const double* gamma, double* rowval, double* out, cudaStream_t st);
+
 }  // namespace ibsn

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "../../include/ibsn.h"
+#include "dense.cuh"
 #include "internal.h"
 
 namespace {
@@ -432,6 +433,76 @@ __global__ void k_ws_adam(int64_t count, float* __restrict__ p, float* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Judge of a start: the semi-dual objective L^0 (Eq. 5 at k = 0), float64.
+// Row i contributes a_i (log a_i + M_i + log S_i) with v_ij = log b_j +
+// (gamma_j - C_ij)/eta, M_i = max_j v_ij and S_i = sum_j exp(v_ij - M_i),
+// accumulated per thread as a running (max, scaled sum) pair and combined
+// across the block in a fixed tree.
+// ---------------------------------------------------------------------------
+constexpr int kSdThreads = 256;
+
+__device__ __forceinline__ void lse_merge(double& m1, double& s1, double m2, double s2) {
+  if (m2 == -INFINITY) return;
+  if (m1 == -INFINITY) {
+    m1 = m2;
+    s1 = s2;
+    return;
+  }
+  if (m2 > m1) {
+    s1 = s1 * exp(m1 - m2) + s2;
+    m1 = m2;
+  } else {
+    s1 += s2 * exp(m2 - m1);
+  }
+}
+
+__global__ void __launch_bounds__(kSdThreads) k_semidual0_rows(ibsn::CostRef cost, int m, int64_t n, double inv_eta,
+                                                               const double* __restrict__ a,
+                                                               const double* __restrict__ logb,
+                                                               const double* __restrict__ gam,
+                                                               double* __restrict__ rowval) {
+  __shared__ double sm[kSdThreads], ss[kSdThreads];
+  const int tid = threadIdx.x;
+  for (int i = blockIdx.x; i < m; i += gridDim.x) {
+    double mx = -INFINITY, s = 0.0;
+    for (int64_t j = tid; j < n; j += kSdThreads) {
+      const double v = logb[j] + ((gam ? gam[j] : 0.0) - ibsn::cost_at(cost, i, j)) * inv_eta;
+      lse_merge(mx, s, v, 1.0);
+    }
+    sm[tid] = mx;
+    ss[tid] = s;
+    __syncthreads();
+    for (int st = kSdThreads / 2; st > 0; st >>= 1) {
+      if (tid < st) {
+        double m1 = sm[tid], s1 = ss[tid];
+        lse_merge(m1, s1, sm[tid + st], ss[tid + st]);
+        sm[tid] = m1;
+        ss[tid] = s1;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) rowval[i] = a[i] * (log(a[i]) + sm[0] + log(ss[0]));
+    __syncthreads();
+  }
+}
+
+// out = eta sum_i rowval_i - b^T gamma (one block, fixed order)
+__global__ void __launch_bounds__(kSdThreads) k_semidual0_finish(int m, int64_t n, double eta,
+                                                                 const double* __restrict__ rowval,
+                                                                 const double* __restrict__ b,
+                                                                 const double* __restrict__ gam,
+                                                                 double* __restrict__ out) {
+  __shared__ double sh[kSdThreads];
+  double r = 0.0, d = 0.0;
+  for (int i = threadIdx.x; i < m; i += kSdThreads) r += rowval[i];
+  if (gam)
+    for (int64_t j = threadIdx.x; j < n; j += kSdThreads) d += b[j] * gam[j];
+  const double rs = block_sum<kSdThreads>(r, sh);
+  const double ds = block_sum<kSdThreads>(d, sh);
+  if (threadIdx.x == 0) *out = eta * rs - ds;
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
@@ -660,3 +731,16 @@ extern "C" int ibsn_ws_adam_step(int64_t count, float* params, float* m1, float*
   ibsn::note_launch();
   return launched();
 }
+
+namespace ibsn {
+
+cudaError_t launch_semidual0(const CostRef& cost, int m, int64_t n, double eta, const double* a, const double* b,
+                             const double* logb, const double* gamma, double* rowval, double* out, cudaStream_t st) {
+  const int blocks = m < 4096 ? m : 4096;
+  k_semidual0_rows<<<blocks, kSdThreads, 0, st>>>(cost, m, n, 1.0 / eta, a, logb, gamma, rowval);
+  k_semidual0_finish<<<1, kSdThreads, 0, st>>>(m, n, eta, rowval, b, gamma, out);
+  note_launch(2);
+  return cudaGetLastError();
+}
+
+}  // namespace ibsn
