@@ -73,6 +73,27 @@ def test_semi_dual_shift_invariance():
     assert abs(L0 - L1) <= 1e-14
 
 
+@pytest.mark.parametrize("shape", [(30, 25), (12, 40)])
+def test_semi_dual_value_matches_entropic_primal_at_optimum(shape):
+    """Strong duality of the k = 0 subproblem (Eq. 2 with X^0 = a b^T, Eq. 5):
+    at the optimal gamma the entropic primal <C, X> + eta KL(X || a b^T) of
+    X = diag(a) P(gamma) equals -L^0(gamma) + eta sum_i a_i log a_i.  Pins the
+    value of L (not only its gradient), including its constant terms."""
+    m, n = shape
+    p = uniform_points_problem(m, n, seed=4, eta=5e-2)
+    logX = O.initial_log_plan(p.a, p.b)
+    g, _, gn = O.sinkhorn_warmup(logX, p.C, p.a, p.b, p.eta, np.zeros(n), 1e-13, 100000)
+    assert gn < 1e-12
+    L = O.semi_dual_objective(logX, p.C, p.a, p.b, p.eta, g)
+    X = p.a[:, None] * O.plan(logX, p.C, p.eta, g)
+    primal = (p.C * X).sum() + p.eta * (X * np.log(X / np.outer(p.a, p.b))).sum()
+    assert abs(primal - (-L + p.eta * (p.a @ np.log(p.a)))) <= 1e-12
+    # and L^0 is minimised there: any other start has a larger value
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        assert O.semi_dual_objective(logX, p.C, p.a, p.b, p.eta, g + rng.normal(0, 0.05, n)) > L
+
+
 def test_best_zeta_is_the_two_dual_minimiser():
     """Eq. 4 zeroes dZ/dzeta of Eq. 3, and L^k = min_zeta Z^k up to the constant eta."""
     C, a, b, eta, logX, gamma = _state(seed=4)
