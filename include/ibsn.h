@@ -288,7 +288,14 @@ int ibsn_plan_pass_noalloc(const ibsn_problem* prob, int64_t k, const double* Ga
 
 /* A batch of point-cloud problems.  Problem q has m[q] source and n[q] target
  * points (1 <= m[q], n[q] <= IBSN_WS_MAX_POINTS); its rows follow those of
- * problems 0..q-1 in the concatenated device arrays. */
+ * problems 0..q-1 in the concatenated device arrays.  1 <= Q <= 65535.
+ *
+ * Errors of every call taking a batch: IBSN_ERR_INVALID_ARG for Q outside
+ * [1, 65535], null m or n arrays, an empty cloud, or a null pointer argument;
+ * IBSN_ERR_UNSUPPORTED for a cloud above IBSN_WS_MAX_POINTS; IBSN_ERR_WORKSPACE
+ * for a null, misaligned (256 B) or too small workspace; IBSN_ERR_CUDA when a
+ * copy or launch fails.  All of these are detected before any device work
+ * except the last.  The caller owns every buffer; the calls allocate nothing. */
 typedef struct ibsn_ws_batch {
   int32_t count;             /* Q >= 1 */
   int32_t reserved_;
@@ -313,10 +320,12 @@ int64_t ibsn_ws_param_count(void);
 /* Fill *hp with the defaults above.  Never fails. */
 void ibsn_ws_adam_default(ibsn_ws_adam* hp);
 
-/* Bytes of device workspace (256-byte aligned) for a batch of these sizes. */
+/* Bytes of device workspace (256-byte aligned) for a batch of these sizes
+ * (host only: reads batch->count, m and n). */
 int ibsn_ws_workspace_size(const ibsn_ws_batch* batch, size_t* bytes);
 
-/* Forward pass: gamma_hat (device, sum n float64, centred per problem). */
+/* Forward pass: gamma_hat (device, sum n float64, centred per problem).
+ * Synchronises the stream once (the row offsets are copied from host). */
 int ibsn_ws_predict(const ibsn_ws_batch* batch, const float* params, double* gamma_hat, void* workspace,
                     size_t workspace_bytes, void* stream);
 
@@ -330,7 +339,9 @@ int ibsn_ws_loss_grad(const ibsn_ws_batch* batch, const float* params, const dou
                       float* grad, double* gamma_hat, void* workspace, size_t workspace_bytes, void* stream);
 
 /* One Adam step t >= 1 on `count` float32 parameters (device arrays params,
- * first and second moments m1, m2, updated in place; gradient grad). */
+ * first and second moments m1, m2, updated in place; gradient grad).  Returns
+ * IBSN_ERR_INVALID_ARG for count < 1, a null pointer, t < 1, lr <= 0, beta1 or
+ * beta2 outside [0, 1) or eps <= 0; IBSN_ERR_CUDA when the launch fails. */
 int ibsn_ws_adam_step(int64_t count, float* params, float* m1, float* m2, const float* grad, int64_t t,
                       const ibsn_ws_adam* hp, void* stream);
 
@@ -341,7 +352,9 @@ int ibsn_ws_adam_step(int64_t count, float* params, float* m1, float* m2, const 
  * nullable); *use_warm = 1 when the warm start's value is finite and smaller.
  * Also reports the gradient norms of Eq. 7 from both starts (plan passes in
  * the working precision of `params`; host outs, nullable).  Uses the solver
- * workspace of ibsn_workspace_size. */
+ * workspace of ibsn_workspace_size.  Errors: IBSN_ERR_INVALID_ARG for a null
+ * prob, params, gamma_hat or use_warm; otherwise those of ibsn_ctx_create
+ * (problem validation, workspace), ibsn_ctx_set_state and ibsn_ctx_plan. */
 int ibsn_judge_warm_start(const ibsn_problem* prob, const ibsn_params* params, const double* gamma_hat,
                           void* workspace, size_t workspace_bytes, double* objective_warm,
                           double* objective_zero, double* grad_norm_warm, double* grad_norm_zero,
