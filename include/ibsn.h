@@ -331,7 +331,8 @@ int ibsn_ws_predict(const ibsn_ws_batch* batch, const float* params, double* gam
 
 /* Forward and backward pass against targets gamma_star (device, sum n; each
  * problem's target is centred inside): the batch loss (host, nullable; the
- * call then synchronises the stream) and its gradient grad (device float32,
+ * stream is synchronised for it, as it is once for the row offsets in every
+ * call) and its gradient grad (device float32,
  * IBSN_WS_PARAM_COUNT, overwritten).  gamma_hat (device, nullable) receives
  * the prediction.  Reductions run in a fixed order: the result does not
  * depend on the launch or on timing. */
