@@ -346,20 +346,23 @@ int ibsn_ws_loss_grad(const ibsn_ws_batch* batch, const float* params, const dou
 int ibsn_ws_adam_step(int64_t count, float* params, float* m1, float* m2, const float* grad, int64_t t,
                       const ibsn_ws_adam* hp, void* stream);
 
-/* Judge a warm start for one problem (Alg. 2 starts from gamma = 0): the
- * semi-dual objective of Eq. 5 at k = 0 (X^0 = a b^T),
+/* Judge a warm start for one problem against a fallback start (Alg. 2
+ * starts from gamma = 0): the semi-dual objective of Eq. 5 at k = 0
+ * (X^0 = a b^T),
  *   L^0(gamma) = -b^T gamma + eta sum_i a_i log sum_j a_i b_j exp((gamma_j - C_ij)/eta),
- * evaluated in float64 at gamma_hat (device n) and at 0 (host outs,
- * nullable); *use_warm = 1 when the warm start's value is finite and smaller.
+ * evaluated in float64 at gamma_hat (device n) and at the fallback
+ * gamma_fallback (device n; NULL means the zero start), reported in
+ * objective_warm / objective_fallback (host outs, nullable); *use_warm = 1 when
+ * the warm start's value is finite and smaller than the fallback's.
  * Also reports the gradient norms of Eq. 7 from both starts (plan passes in
  * the working precision of `params`; host outs, nullable).  Uses the solver
  * workspace of ibsn_workspace_size.  Errors: IBSN_ERR_INVALID_ARG for a null
  * prob, params, gamma_hat or use_warm; otherwise those of ibsn_ctx_create
  * (problem validation, workspace), ibsn_ctx_set_state and ibsn_ctx_plan. */
 int ibsn_judge_warm_start(const ibsn_problem* prob, const ibsn_params* params, const double* gamma_hat,
-                          void* workspace, size_t workspace_bytes, double* objective_warm,
-                          double* objective_zero, double* grad_norm_warm, double* grad_norm_zero,
-                          int32_t* use_warm, void* stream);
+                          const double* gamma_fallback, void* workspace, size_t workspace_bytes,
+                          double* objective_warm, double* objective_fallback, double* grad_norm_warm,
+                          double* grad_norm_fallback, int32_t* use_warm, void* stream);
 
 #ifdef __cplusplus
 }

@@ -84,7 +84,7 @@ _SIGS = {
     "ibsn_ws_adam_step": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                     C.POINTER(IbsnWsAdam), C.c_void_p]),
     "ibsn_judge_warm_start": (C.c_int, [C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.c_void_p, C.c_void_p,
-                                        C.c_size_t, c_double_p, c_double_p, c_double_p, c_double_p,
+                                        C.c_void_p, C.c_size_t, c_double_p, c_double_p, c_double_p, c_double_p,
                                         C.POINTER(C.c_int32), C.c_void_p]),
     "ibsn_ctx_create": (C.c_int, [C.POINTER(IbsnProblem), C.POINTER(IbsnParams), C.c_void_p, C.c_size_t,
                                   C.c_void_p, C.POINTER(C.c_void_p)]),

@@ -1250,13 +1250,15 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
   return status;
 }
 
-// Warm start or zero start (Alg. 2 starts from gamma = 0): the start with the
-// smaller semi-dual objective L^0 (Eq. 5 at k = 0) wins; a non-finite value
-// never wins.  The plan-pass gradient norms (Eq. 7) from both starts are
-// reported alongside.
+// Warm start or fallback start (Alg. 2 starts from gamma = 0; the fallback is
+// that zero start or a given potential): the start with the smaller
+// semi-dual objective L^0 (Eq. 5 at k = 0) wins; a non-finite value never
+// wins.  The plan-pass gradient norms (Eq. 7) from both starts are reported
+// alongside.
 int ibsn_judge_warm_start(const ibsn_problem* prob, const ibsn_params* params, const double* gamma_hat,
-                          void* workspace, size_t workspace_bytes, double* objective_warm, double* objective_zero,
-                          double* grad_norm_warm, double* grad_norm_zero, int32_t* use_warm, void* stream) {
+                          const double* gamma_fallback, void* workspace, size_t workspace_bytes,
+                          double* objective_warm, double* objective_fallback, double* grad_norm_warm,
+                          double* grad_norm_fallback, int32_t* use_warm, void* stream) {
   if (!prob || !params || !gamma_hat || !use_warm) return IBSN_ERR_INVALID_ARG;
   ibsn_ctx* X = nullptr;
   RT(ctx_create_impl(prob, params, workspace, workspace_bytes, (cudaStream_t)stream, &X));
@@ -1271,15 +1273,16 @@ int ibsn_judge_warm_start(const ibsn_problem* prob, const ibsn_params* params, c
   CK(launch_semidual0(X->cost, X->m, X->n, X->eta, X->a, X->b, X->logb, gamma_hat, X->er, X->scal + S_TMP, X->st));
   RT(read_scal(X));
   const double Lw = X->h_scal[S_TMP];
-  RT(ibsn_ctx_set_state(X, 0, nullptr, nullptr, prec));
+  RT(ibsn_ctx_set_state(X, 0, nullptr, gamma_fallback, prec));
   RT(ibsn_ctx_plan(X, nullptr, &gz));
-  CK(launch_semidual0(X->cost, X->m, X->n, X->eta, X->a, X->b, X->logb, nullptr, X->er, X->scal + S_TMP, X->st));
+  CK(launch_semidual0(X->cost, X->m, X->n, X->eta, X->a, X->b, X->logb, gamma_fallback, X->er, X->scal + S_TMP,
+                      X->st));
   RT(read_scal(X));
   const double Lz = X->h_scal[S_TMP];
   if (objective_warm) *objective_warm = Lw;
-  if (objective_zero) *objective_zero = Lz;
+  if (objective_fallback) *objective_fallback = Lz;
   if (grad_norm_warm) *grad_norm_warm = gw;
-  if (grad_norm_zero) *grad_norm_zero = gz;
+  if (grad_norm_fallback) *grad_norm_fallback = gz;
   *use_warm = (std::isfinite(Lw) && Lw < Lz) ? 1 : 0;
   return IBSN_OK;
 }

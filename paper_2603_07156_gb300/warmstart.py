@@ -136,27 +136,32 @@ class Trainer:
         return loss
 
 
-def judge(problem: Problem, prm: N.IbsnParams, gamma_hat: torch.Tensor, workspace=None, stream=None) -> dict:
+def judge(problem: Problem, prm: N.IbsnParams, gamma_hat: torch.Tensor, workspace=None, stream=None,
+          fallback: torch.Tensor | None = None) -> dict:
     """ibsn_judge_warm_start: the semi-dual objective L^0 (Eq. 5) and the
-    gradient norm from gamma_hat and from 0; use_warm when L^0 is smaller."""
+    gradient norm from gamma_hat and from the fallback start (zero, or the
+    given potential); use_warm when gamma_hat's L^0 is smaller."""
     ws = workspace if workspace is not None else alloc_workspace(problem, prm)
     lw, lz, gw, gz = (C.c_double(0.0) for _ in range(4))
     use = C.c_int32(0)
     pr = problem.struct()
-    N.check(N.load().ibsn_judge_warm_start(C.byref(pr), C.byref(prm), _ptr(gamma_hat), _ptr(ws), ws.numel(),
+    N.check(N.load().ibsn_judge_warm_start(C.byref(pr), C.byref(prm), _ptr(gamma_hat), _ptr(fallback), _ptr(ws),
+                                           ws.numel(),
                                            C.byref(lw), C.byref(lz), C.byref(gw), C.byref(gz), C.byref(use),
                                            _stream_ptr(stream)), "ibsn_judge_warm_start")
-    return dict(use_warm=bool(use.value), objective_warm=lw.value, objective_zero=lz.value,
-                grad_norm_warm=gw.value, grad_norm_zero=gz.value)
+    return dict(use_warm=bool(use.value), objective_warm=lw.value, objective_fallback=lz.value,
+                grad_norm_warm=gw.value, grad_norm_fallback=gz.value)
 
 
-def solve_warm(problem: Problem, prm: N.IbsnParams, gamma_hat: torch.Tensor, workspace=None, **kw) -> dict:
-    """Judge gamma_hat against the zero start, then solve from the winner.
-    The result carries warm_used and the judge's objectives and gradient norms."""
+def solve_warm(problem: Problem, prm: N.IbsnParams, gamma_hat: torch.Tensor, workspace=None,
+               fallback: torch.Tensor | None = None, **kw) -> dict:
+    """Judge gamma_hat against the fallback start (zero, or the given
+    potential), then solve from the winner.  The result carries warm_used
+    and the judge's objectives and gradient norms."""
     ws = workspace if workspace is not None else alloc_workspace(problem, prm)
-    j = judge(problem, prm, gamma_hat, ws)
+    j = judge(problem, prm, gamma_hat, ws, fallback=fallback)
     p2 = N.IbsnParams.from_buffer_copy(prm)
-    p2.gamma0 = _ptr(gamma_hat) if j["use_warm"] else None
+    p2.gamma0 = _ptr(gamma_hat) if j["use_warm"] else _ptr(fallback)
     res = solve(problem, p2, workspace=ws, **kw)
     res.update(warm_used=j["use_warm"], **{k: v for k, v in j.items() if k != "use_warm"})
     return res
