@@ -336,10 +336,10 @@ def run_warmstart(args):
     t0 = time.perf_counter()
     train = [warmstart_gmm_problem(args.ws_train_n, 10_000 + s) for s in range(args.ws_train)]
     targets, solved = [], 0
-    for p in train:
-        r = G.solve(gpu(p), prm)
-        targets.append(r["gamma"])
-        solved += int(r["converged"])
+    for k in range(0, len(train), 32):  # training solves run concurrently, 32 problems per batched call
+        outs = G.solve_batch([gpu(p) for p in train[k:k + 32]], prm, threads=args.batch_threads)
+        targets += [r["gamma"] for r in outs]
+        solved += sum(int(r["converged"]) for r in outs)
     torch.cuda.synchronize(dev)
     t_solves = time.perf_counter() - t0
     batches = []
