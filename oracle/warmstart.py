@@ -3,8 +3,8 @@
 The paper starts every solve from gamma^{0,0} = 0 (Alg. 2).  The learned warm
 start replaces that start by a prediction gamma_hat of the optimal dual
 potential (cost units, centred) made by a small network from the two point
-clouds and their marginals; the plain start stays as the fallback and one
-plan pass each decides between them (smaller ||grad||, Eq. 7).
+clouds and their marginals; the plain start stays as the fallback, and the
+start with the smaller semi-dual objective L^0 (Eq. 5 at k = 0) is kept.
 
 Network (three layers of width 128; weights are bfloat16 values):
   source point i:  f_i = [x_i1, x_i2, m a_i],  e_i = relu(W_s f_i + b_s)
