@@ -66,6 +66,7 @@ def parse():
                     help="grid: the 16384-bin headline; batch64: 64 uneven point-cloud problems "
                          "(m, n ~ U{500..5000}) solved by one ibsn_solve_batch call")
     ap.add_argument("--batch-threads", type=int, default=8)
+    ap.add_argument("--verbose", type=int, default=0, help="per-outer log lines of the solver on stderr")
     return ap.parse_args()
 
 
@@ -429,7 +430,7 @@ def main():
         extra["max_outer"] = args.max_outer
     if args.nnz_cap > 0:
         extra["nnz_cap"] = args.nnz_cap
-    prm = G.params(precision=args.precision, profile=1, **extra)
+    prm = G.params(precision=args.precision, profile=1, verbose=args.verbose, **extra)
     ws = G.alloc_workspace(prob, prm)
     stream = torch.cuda.current_stream(dev)
 

@@ -245,20 +245,46 @@ int ibsn_ctx_certify(ibsn_ctx* ctx, double* primal, double* dual, double* rel_ga
  * process that must keep its device footprint fixed after start-up).
  *
  * Computes, for the outer iterate given by (k, Gamma, gamma) exactly as
- * ibsn_ctx_set_state does, the column sums colsum = P^k(gamma)^T a (device
- * float64, n) of the plan of Eq. 6 and, if grad_norm is non-NULL, ||colsum - b||
- * (host; the call then synchronises the stream).  Arithmetic is float64; the
- * exponent is rebuilt from the cost for every entry.  Gamma and gamma are
- * device n-vectors, either may be NULL (zero).
+ * ibsn_ctx_set_state does, the column sums colsum = P^T a (device float64, n)
+ * of that iterate's row-normalised plan P, whose entry (i, j) is proportional
+ * to b_j exp((Gamma_j + gamma_j - (k+1) C_ij)/eta), and, if grad_norm is
+ * non-NULL, ||colsum - b|| (host; the call then synchronises the stream).
+ * Arithmetic is float64; the exponent is rebuilt from the cost for every
+ * entry.  Gamma and gamma are device n-vectors, either may be NULL (zero).
+ *
+ * Unlike ibsn_ctx_create, this call does not validate the problem's values:
+ * the caller must pass a, b > 0 summing to 1 and a finite C >= 0 (a
+ * non-positive b_j, for instance, yields NaN results with status IBSN_OK).
  *
  * Scratch lives in one fixed array inside the library (about 4.1 MiB on every
  * GPU that loads it, held until the process exits); the call allocates
  * nothing.  Limits: n <= 4096 columns (larger n returns IBSN_ERR_UNSUPPORTED),
  * any m.  All calls share that array: calls whose kernels overlap on the GPU
  * race, so serialise them on one stream.  The first call on each device looks
- * up the array's device address; make it before any CUDA stream capture. */
+ * up the array's device address and caches it for the life of the process;
+ * make it before any CUDA stream capture, and do not use this call after a
+ * cudaDeviceReset (or any teardown of the device's primary context): the
+ * cached address would belong to the old context. */
 int ibsn_plan_pass_noalloc(const ibsn_problem* prob, int64_t k, const double* Gamma, const double* gamma,
                            double* colsum, double* grad_norm, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Check of the bounded device waits.  The paper has no counterpart: the
+ * persistent PCG kernels (Newton direction of Alg. 2) synchronise their blocks
+ * with grid-wide barriers whose waits are bounded by params.wait_timeout_s;
+ * this call runs that same barrier on its own so that a caller can check, on
+ * its GPU, that a wait which can never complete ends with an error instead of
+ * a hang.
+ *
+ * Launches `blocks` co-resident blocks (2 <= blocks <= the device's SM count)
+ * that meet at one grid barrier.  With withhold = 0 all arrive and the call
+ * returns IBSN_OK; with withhold != 0 block 0 leaves without arriving, the
+ * others wait timeout_s seconds (0 < timeout_s <= 10), record the time-out and
+ * return, and the call returns IBSN_ERR_TIMEOUT; the CUDA context stays
+ * usable.  scratch: caller device memory of at least 8 bytes, 8-byte aligned
+ * (overwritten).  Synchronises the stream.  IBSN_ERR_INVALID_ARG for bad
+ * arguments, IBSN_ERR_CUDA when the launch fails. */
+int ibsn_wait_probe(int blocks, int withhold, double timeout_s, void* scratch, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start.  The paper starts every solve from gamma^{0,0} = 0

@@ -103,6 +103,7 @@ _SIGS = {
     "ibsn_ctx_stop_check": (C.c_int, [C.c_void_p, c_double_p]),
     "ibsn_ctx_certify": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p, c_double_p, C.c_void_p,
                                    C.c_void_p]),
+    "ibsn_wait_probe": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "ibsn_plan_pass_noalloc": (C.c_int, [C.POINTER(IbsnProblem), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                          c_double_p, C.c_void_p]),
 }

@@ -12,6 +12,7 @@
 #include <atomic>
 #include <mutex>
 
+#include "../../include/ibsn.h"
 #include "common.cuh"
 #include "internal.h"
 
@@ -904,3 +905,41 @@ cudaError_t launch_pcg(const SparseBufs& S, const PcgBufs& B, int m, int64_t n, 
 }
 
 }  // namespace ibsn
+
+// ---------------------------------------------------------------------------
+// Check of the bounded grid-wide wait that the persistent PCG kernels use
+// (grid_barrier).  Every block except, when `withhold` is set, block 0 arrives
+// at one grid barrier; with a block withheld the count can never reach its
+// target, so the others wait out `budget_ns`, record kDevTimeout and return.
+namespace ibsn {
+namespace {
+__global__ void k_wait_probe(unsigned int* count, int* err, int withhold, unsigned long long budget_ns) {
+  if (withhold && blockIdx.x == 0) return;
+  grid_barrier(count, nullptr, err, budget_ns);
+}
+}  // namespace
+}  // namespace ibsn
+
+extern "C" int ibsn_wait_probe(int blocks, int withhold, double timeout_s, void* scratch, void* stream) {
+  using namespace ibsn;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IBSN_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IBSN_ERR_CUDA;
+  if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 7u) || blocks < 2 || blocks > nsm ||
+      !(timeout_s > 0.0) || timeout_s > 10.0)
+    return IBSN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned int* count = static_cast<unsigned int*>(scratch);
+  int* err = reinterpret_cast<int*>(count + 1);
+  if (cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) return IBSN_ERR_CUDA;
+  int wh = withhold ? 1 : 0;
+  unsigned long long budget = (unsigned long long)(timeout_s * 1e9);
+  void* args[] = {(void*)&count, (void*)&err, (void*)&wh, (void*)&budget};
+  if (cudaLaunchCooperativeKernel((const void*)k_wait_probe, dim3(blocks), dim3(32), args, 0, st) != cudaSuccess)
+    return IBSN_ERR_CUDA;
+  note_launch();
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return IBSN_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return IBSN_ERR_CUDA;
+  return h == kDevTimeout ? IBSN_ERR_TIMEOUT : IBSN_OK;
+}

@@ -66,11 +66,55 @@ def test_noalloc_matches_workspace_path_twice(which):
     gam = torch.tensor(rng.normal(0, 0.5 * prob.eta, prob.n), device="cuda")
     k = 3
     c_ref, gn_ref = _reference(gp, k, Gam, gam)
+    # the oracle's plan at an iterate whose cumulative potential is Gamma:
+    # k outer updates by Gamma / k each (Alg. 2 outer update)
+    from oracle import ibsn as O
+    Gh, gh = Gam.cpu().numpy(), gam.cpu().numpy()
+    logX = O.initial_log_plan(prob.a, prob.b)
+    for _ in range(k):
+        logX = np.log(prob.a)[:, None] + O.log_plan(logX, prob.C, prob.eta, Gh / k)
+    c_orc = O.plan(logX, prob.C, prob.eta, gh).T @ prob.a
     pr = gp.struct()
     for _ in range(2):  # the shared scratch keeps the previous call's contents
         c, gn = _noalloc(lib, pr, k, Gam, gam, prob.n)
         assert np.abs(c - c_ref).max() <= 1e-11 * prob.b.max()
+        assert np.abs(c - c_orc).max() <= 1e-11 * prob.b.max()
         assert abs(gn - gn_ref) <= 1e-10 * max(gn_ref, 1e-12)
+
+
+def test_noalloc_matches_oracle_at_the_size_limit():
+    """n = 4096 (the largest accepted width) and m = 1000 rows: the finish
+    kernel loops over four columns per thread and every one of the 128 column
+    partials of the scratch is used.  Compared with the workspace path and with
+    the float64 oracle's column sums P^T a of the row-normalised plan (Eqs. 6-7)
+    at the same outer iterate, on two calls in a row."""
+    import paper_2603_07156_gb300 as G
+    from oracle import ibsn as O
+    from paper_2603_07156_gb300 import _native as N
+    lib = N.load()
+    prob = uniform_points_problem(1000, 4096, seed=94, eta=1e-2)
+    gp = G.Problem(a=torch.tensor(prob.a, device="cuda"), b=torch.tensor(prob.b, device="cuda"), eta=prob.eta,
+                   C=torch.tensor(prob.C, device="cuda"))
+    rng = np.random.default_rng(95)
+    k = 2
+    gs = [rng.normal(0, 0.3 * prob.eta, prob.n) for _ in range(k)]
+    gamma = rng.normal(0, 0.3 * prob.eta, prob.n)
+    # oracle: explicit outer recursion log X^{j+1} = log(diag(a) P^j(g_j)) from X^0 = a b^T
+    logX = O.initial_log_plan(prob.a, prob.b)
+    for g in gs:
+        logX = np.log(prob.a)[:, None] + O.log_plan(logX, prob.C, prob.eta, g)
+    P = O.plan(logX, prob.C, prob.eta, gamma)
+    c_orc = P.T @ prob.a
+    gn_orc = float(np.linalg.norm(O.gradient(P, prob.a, prob.b)))
+    Gam = torch.tensor(np.sum(gs, axis=0), device="cuda")
+    gam = torch.tensor(gamma, device="cuda")
+    c_ref, gn_ref = _reference(gp, k, Gam, gam)
+    pr = gp.struct()
+    for _ in range(2):
+        c, gn = _noalloc(lib, pr, k, Gam, gam, prob.n)
+        assert np.abs(c - c_ref).max() <= 1e-11 * prob.b.max()
+        assert np.abs(c - c_orc).max() <= 1e-11 * prob.b.max()
+        assert abs(gn - gn_orc) <= 1e-10 * gn_orc
 
 
 def test_noalloc_refuses_oversized_problems():

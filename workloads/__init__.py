@@ -10,6 +10,7 @@ from .generators import (  # noqa: F401
     uniform_points_problem,
     gmm_points_problem,
     grid_problem,
+    grid_marginals,
     batched_problems,
     batched_points,
     warmstart_gmm_problem,

@@ -151,22 +151,26 @@ def _gaussian_blur(img: np.ndarray, sigma: float) -> np.ndarray:
     return out
 
 
-def grid_problem(h: int, w: int, seed: int, sigma: float = 4.0, eta: float = 1e-3,
-                 cost_dtype=np.float64) -> OTProblem:
-    """Smoothed random fields on an h x w grid; C = squared grid distance / max.
-
-    Draw order: source noise (h*w), target noise (h*w).  Marginals are
-    blur(noise) + 1e-6, normalised.  The cost scale is 1 / ((h-1)^2 + (w-1)^2).
-    """
+def grid_marginals(h: int, w: int, seed: int, sigma: float = 4.0):
+    """The marginals and cost scale of grid_problem without the (h w)^2 cost
+    matrix: (a, b, scale).  Draw order: source noise (h*w), target noise (h*w).
+    Marginals are blur(noise) + 1e-6, normalised; scale = 1 / ((h-1)^2 + (w-1)^2)."""
     rng = np.random.default_rng(seed)
     src = _gaussian_blur(rng.uniform(0.0, 1.0, size=(h, w)), sigma) + 1e-6
     dst = _gaussian_blur(rng.uniform(0.0, 1.0, size=(h, w)), sigma) + 1e-6
     a = (src / src.sum()).ravel()
     b = (dst / dst.sum()).ravel()
-    raw = grid_sq_cost(h, w)
     mx = float((h - 1) ** 2 + (w - 1) ** 2)
     scale = 1.0 / mx if mx > 0 else 1.0
-    C = raw * scale
+    return a, b, scale
+
+
+def grid_problem(h: int, w: int, seed: int, sigma: float = 4.0, eta: float = 1e-3,
+                 cost_dtype=np.float64) -> OTProblem:
+    """Smoothed random fields on an h x w grid; C = squared grid distance / max
+    (marginals and scale from grid_marginals)."""
+    a, b, scale = grid_marginals(h, w, seed, sigma)
+    C = grid_sq_cost(h, w) * scale
     return OTProblem(C=C.astype(cost_dtype), a=a, b=b, eta=eta, name=f"grid{h}x{w}_s{seed}",
                      grid=(h, w), cost_scale=scale)
 
