@@ -99,6 +99,15 @@ typedef struct ibsn_params {
   int32_t sparsify;          /* 1 = IBSN (Alg. 1); 0 = IBN, dense Hessian (App. C.3) */
   int32_t verbose;           /* per-outer log lines on stderr */
   int32_t profile;           /* 1: time every pass kind with CUDA events (ibsn_result.pass_ms) */
+  double eot_gtol;           /* eot mode: stop once ||g|| < eot_gtol (1e-9, App. C.4) */
+  int32_t eot;               /* 1 = (E)IBSN (App. C.4): one entropic subproblem with
+                                X^0 = 1 1^T (not a b^T), Sinkhorn warm-up, then at most
+                                max_newton Newton steps until ||g|| < eot_gtol; no
+                                outer update.  The result's gamma is the semi-dual
+                                solution of that subproblem; primal/dual/rel_gap
+                                certify its rounded plan for the LP of Eq. 1; status
+                                IBSN_OK when the gradient test passed.  0 = IBSN. */
+  int32_t reserved_;
 } ibsn_params;
 
 /* Result of ibsn_solve.  Output vectors are optional caller buffers. */

@@ -397,3 +397,59 @@ def ibsn(C, a, b, params: IBSNParams, gamma0=None, record=False) -> IBSNResult:
                       kkt=kkt_residual(X, C, a, b, gamma, zeta), outer_iters=k + 1,
                       newton_iters=tot_newton, cg_iters=tot_cg, sinkhorn_iters=tot_sk,
                       converged=converged, history=hist)
+
+
+# ----------------------------------------------------------------------------
+# (E)IBSN (App. C.4): the inner solve alone on one entropic subproblem
+# ----------------------------------------------------------------------------
+
+@dataclass
+class EIBSNResult:
+    gamma: np.ndarray
+    plan: np.ndarray
+    gnorm: float
+    newton_iters: int
+    cg_per_direction: list
+    sinkhorn_iters: int
+    converged: bool
+
+
+def eibsn(C, a, b, params: IBSNParams, gtol: float = 1e-9, gamma0=None) -> EIBSNResult:
+    """(E)IBSN of App. C.4: Alg. 2's inner loop on the single subproblem with
+    X^k fixed at 1 1^T (the entropic OT problem with cost C), no outer update.
+
+    Sinkhorn warm-up to ||g|| < sinkhorn_tol, centring, then Newton steps
+    (Alg. 1 sparsification, shifted Newton system by PCG, Armijo) until
+    ||g|| < gtol or max_newton steps.  The CG tolerance is reading R3 with the
+    gate gtol in place of mu_k.
+    """
+    C = np.asarray(C, dtype=np.float64)
+    m, n = C.shape
+    eta = params.eta
+    logX = np.zeros((m, n))  # X = 1 1^T
+    gamma = np.zeros(n) if gamma0 is None else np.asarray(gamma0, dtype=np.float64).copy()
+    gamma, sk_it, _ = sinkhorn_warmup(logX, C, a, b, eta, gamma, params.sinkhorn_tol, params.max_sinkhorn)
+    gamma = gamma - gamma.mean()
+    cgs = []
+    converged = False
+    v = 0
+    for v in range(params.max_newton + 1):
+        P = plan(logX, C, eta, gamma)
+        g = gradient(P, a, b)
+        gnorm = float(np.linalg.norm(g))
+        if gnorm < gtol:
+            converged = True
+            break
+        if v == params.max_newton:
+            break
+        if params.sparsify:
+            rho = sparsification_threshold(eta, m, n, gnorm)
+            H = sparsified_hessian(sparsify_plan(P, a, rho), a, eta)
+        else:
+            H = hessian(P, a, eta)
+        delta, cg_it = newton_direction(H, g, params.cg_rtol, params.max_cg, gtol)
+        cgs.append(cg_it)
+        t, _, _ = armijo(logX, C, a, b, eta, gamma, delta, g, params.sigma, params.beta, params.max_armijo)
+        gamma = gamma + t * delta
+    return EIBSNResult(gamma=gamma, plan=P, gnorm=gnorm, newton_iters=len(cgs), cg_per_direction=cgs,
+                       sinkhorn_iters=sk_it, converged=converged)

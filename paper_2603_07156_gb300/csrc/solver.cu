@@ -738,6 +738,56 @@ int do_certify(ibsn_ctx* X, Cert* out, double* plan, double* zeta) {
   return IBSN_OK;
 }
 
+struct NewtonStats {
+  int newton = 0, cg = 0, armijo = 0;
+  int64_t max_nnz = 0;
+};
+
+// One Newton step of Alg. 2 at the current gamma: threshold rho = eta ||g|| / (m n)
+// and sparsified Hessian (Alg. 1), Newton direction by PCG, Armijo backtracking
+// in difference form, and the move gamma += t Delta (with its plan pass).
+int newton_step(ibsn_ctx* X, const ibsn_params& P, double gate, int k, int v, NewtonStats* ns) {
+  const double mn = (double)X->m * (double)X->n;
+  const double gn = X->gn;
+  const double rho = P.sparsify ? X->eta * gn / mn : 0.0;
+  RT(do_sparsify(X, rho));
+  ns->max_nnz = std::max(ns->max_nnz, X->nnz);
+  // forcing term ||g||, relaxed to the accuracy at which the linear model
+  // predicts the next gradient below the gate (reading R3)
+  double rtol = gn > 0.0 ? std::min(P.cg_rtol, std::max(gn, 0.25 * gate / gn)) : P.cg_rtol;
+  if (X->prec != 0) rtol = std::max(rtol, P.cg_rtol_floor_mixed);  // float32 Hessian values
+  int cgit = 0;
+  double cgres = 0.0;
+  if (P.verbose > 1) CK(launch_len_stats(X->sp, X->m, X->n, X->scal, X->st));
+  RT(do_direction(X, gn, rtol, P.max_cg, &cgit, &cgres));
+  ns->cg += cgit;
+  if (P.verbose > 1)
+    fprintf(stderr, "[ibsn]   newton k=%d v=%d |g|=%.3e nnz=%lld maxrow=%d maxcol=%d cg=%d rtol=%.1e\n", k, v, gn,
+            (long long)X->nnz, (int)X->h_scal[S_MAXROW], (int)X->h_scal[S_MAXCOL], cgit, rtol);
+  // trials whose largest exponent change t max|Delta|/eta exceeds the pass
+  // range are rejected unevaluated (exp would overflow in that precision)
+  const double dmax = X->h_scal[S_DELTAMAX];
+  const double range = X->prec == 0 ? 600.0 : (X->prec == 1 ? 60.0 : 30.0);
+  double t = 1.0, dL = 0.0, slope = 0.0;
+  bool evaluated = false;
+  for (int tr = 0; tr < P.max_armijo; ++tr) {
+    const bool last = tr + 1 == P.max_armijo;
+    if (t * dmax <= range || last) {
+      RT(do_armijo_trial(X, t, &dL, &slope));
+      evaluated = true;
+      ++ns->armijo;
+      if (std::isfinite(dL) && dL <= P.sigma * t * slope) break;
+    }
+    if (!last) t *= P.beta;
+  }
+  // after max_armijo trials the last step tried is taken (reading R4)
+  if (!evaluated || !std::isfinite(dL)) return IBSN_ERR_NUMERICAL;
+  RT(do_accept(X, t));
+  if (!std::isfinite(X->gn)) return IBSN_ERR_NUMERICAL;
+  ++ns->newton;
+  return IBSN_OK;
+}
+
 int outer_advance(ibsn_ctx* X, int new_prec) {
   // Gamma^{k+1} = Gamma^k + gamma^{k,fin}; k += 1; rebuild the anchor
   k_axpy<<<(unsigned)((X->n + 255) / 256), 256, 0, X->st>>>(X->n, 1.0, X->gam, X->Gam);
@@ -902,6 +952,8 @@ void ibsn_params_default(ibsn_params* p) {
   p->polish = 1;
   p->sparsify = 1;
   p->verbose = 0;
+  p->eot = 0;
+  p->eot_gtol = 1e-9;
 }
 
 int ibsn_workspace_size(const ibsn_problem* prob, const ibsn_params* params, size_t* bytes) {
@@ -1095,74 +1147,74 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
   } guard{X};
   const ibsn_params& P = *params;
   const int64_t m = X->m, n = X->n;
-  const double mn = (double)m * (double)n;
   const double floor32 = 32.0 * std::ldexp(1.0, -24);  // relative float32 noise of a column sum
+  // (E)IBSN: the single entropic subproblem with X^0 = 1 1^T instead of a b^T;
+  // the row factor a_i does not change the plan, the column factor b_j is
+  // dropped from the anchored exponent
+  if (P.eot) CK(cudaMemsetAsync(X->logb, 0, sizeof(double) * n, X->st));
   // initial state: k = 0, Gamma = 0, gamma = gamma0 or 0
   RT(ibsn_ctx_set_state(X, 0, nullptr, P.gamma0, X->prec));
-  int tot_newton = 0, tot_cg = 0, tot_sk = 0, tot_armijo = 0, polish_outer = 0;
-  int64_t max_nnz = 0;
+  NewtonStats ns;
+  int tot_sk = 0, polish_outer = 0;
   Cert cert{1e300, -1e300, 1e300, 0, 0};
   double best_gap = 1e300;
   int stall = 0;
   int status = IBSN_NOT_CONVERGED;
   int k = 0;
-  double bnorm = -1.0;
-  for (k = 0; k < P.max_outer; ++k) {
+  double bnorm = 0.0;
+  {
+    std::vector<double> hb(n);
+    CK(cudaMemcpyAsync(hb.data(), X->b, sizeof(double) * n, cudaMemcpyDeviceToHost, X->st));
+    CK(cudaStreamSynchronize(X->st));
+    for (double v : hb) bnorm += v * v;
+    bnorm = std::sqrt(bnorm);  // ||b||_2 for the float32 gradient floor
+  }
+  if (P.eot) {
+    // Sinkhorn warm-up, then Newton steps until ||g|| < eot_gtol or max_newton
+    // steps (App. C.4).  Float32 passes cannot resolve ||g|| below their noise
+    // floor: there (or once a step no longer halves ||g||) a mixed solve with
+    // polish continues in float-float passes.
+    int sk = 0;
+    RT(do_sinkhorn(X, P.sinkhorn_tol, P.max_sinkhorn, &sk));
+    tot_sk += sk;
+    if (!std::isfinite(X->gn)) return IBSN_ERR_NUMERICAL;
+    double gn_before = 1e300;
+    for (int v = 0; v < P.max_newton; ++v) {
+      if (X->gn < P.eot_gtol) {
+        status = IBSN_OK;
+        break;
+      }
+      if (X->prec == 1 && X->have_ff && (X->gn < floor32 * bnorm || X->gn > 0.5 * gn_before)) {
+        X->prec = 2;
+        RT(do_reanchor(X));
+        RT(do_plan(X));
+        if (X->gn < P.eot_gtol) {
+          status = IBSN_OK;
+          break;
+        }
+      }
+      gn_before = X->gn;
+      RT(newton_step(X, P, P.eot_gtol, 0, v, &ns));
+      if (P.verbose)
+        fprintf(stderr, "[ibsn] eot v=%d prec=%s |g|=%.3e nnz=%lld\n", v,
+                X->prec == 0 ? "f64" : (X->prec == 1 ? "f32" : "ff"), X->gn, (long long)X->nnz);
+    }
+    if (status != IBSN_OK && X->gn < P.eot_gtol) status = IBSN_OK;
+    if (X->prec == 2) polish_outer = 1;
+    RT(do_certify(X, &cert, nullptr, nullptr));
+    k = 1;
+  }
+  for (k = P.eot ? 1 : 0; !P.eot && k < P.max_outer; ++k) {
     const double mu = std::max(P.mu0 / ((double)(k + 1) * (double)(k + 1)), P.mu_min);
     int sk = 0;
     RT(do_sinkhorn(X, P.sinkhorn_tol, P.max_sinkhorn, &sk));
     tot_sk += sk;
     if (!std::isfinite(X->gn)) return IBSN_ERR_NUMERICAL;
-    if (bnorm < 0) {
-      // ||b||_2 for the float32 gradient floor
-      bnorm = 0.0;
-      std::vector<double> hb(n);
-      CK(cudaMemcpyAsync(hb.data(), X->b, sizeof(double) * n, cudaMemcpyDeviceToHost, X->st));
-      CK(cudaStreamSynchronize(X->st));
-      for (double v : hb) bnorm += v * v;
-      bnorm = std::sqrt(bnorm);
-    }
     const double gate = X->prec == 1 ? std::max(mu, floor32 * bnorm) : mu;
     int v = 0;
-    double gn_prev = 1e300;
     for (v = 0; v < P.max_newton; ++v) {
       const double gn = X->gn;
-      const double rho = P.sparsify ? X->eta * gn / mn : 0.0;
-      RT(do_sparsify(X, rho));
-      max_nnz = std::max(max_nnz, X->nnz);
-      // forcing term ||g||, relaxed to the accuracy at which the linear model
-      // predicts the next gradient below the gate (reading R3)
-      double rtol = gn > 0.0 ? std::min(P.cg_rtol, std::max(gn, 0.25 * gate / gn)) : P.cg_rtol;
-      if (X->prec != 0) rtol = std::max(rtol, P.cg_rtol_floor_mixed);  // float32 Hessian values
-      int cgit = 0;
-      double cgres = 0.0;
-      if (P.verbose > 1) CK(launch_len_stats(X->sp, X->m, X->n, X->scal, X->st));
-      RT(do_direction(X, gn, rtol, P.max_cg, &cgit, &cgres));
-      tot_cg += cgit;
-      if (P.verbose > 1)
-        fprintf(stderr, "[ibsn]   newton k=%d v=%d |g|=%.3e nnz=%lld maxrow=%d maxcol=%d cg=%d rtol=%.1e\n", k, v, gn,
-                (long long)X->nnz, (int)X->h_scal[S_MAXROW], (int)X->h_scal[S_MAXCOL], cgit, rtol);
-      // trials whose largest exponent change t max|Delta|/eta exceeds the pass
-      // range are rejected unevaluated (exp would overflow in that precision)
-      const double dmax = X->h_scal[S_DELTAMAX];
-      const double range = X->prec == 0 ? 600.0 : (X->prec == 1 ? 60.0 : 30.0);
-      double t = 1.0, dL = 0.0, slope = 0.0;
-      bool evaluated = false;
-      for (int tr = 0; tr < P.max_armijo; ++tr) {
-        const bool last = tr + 1 == P.max_armijo;
-        if (t * dmax <= range || last) {
-          RT(do_armijo_trial(X, t, &dL, &slope));
-          evaluated = true;
-          ++tot_armijo;
-          if (std::isfinite(dL) && dL <= P.sigma * t * slope) break;
-        }
-        if (!last) t *= P.beta;
-      }
-      // after max_armijo trials the last step tried is taken (reading R4)
-      if (!evaluated || !std::isfinite(dL)) return IBSN_ERR_NUMERICAL;
-      RT(do_accept(X, t));
-      if (!std::isfinite(X->gn)) return IBSN_ERR_NUMERICAL;
-      ++tot_newton;
+      RT(newton_step(X, P, gate, k, v, &ns));
       if (X->gn < gate) {
         double dphi = 0.0;
         RT(do_stop(X, &dphi));
@@ -1178,9 +1230,7 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
           break;
         }
       }
-      gn_prev = gn;
     }
-    (void)gn_prev;
     // certificate at X^{k+1} = diag(a) P^k(gamma^{k,fin}); with float32 passes
     // it only steers the switch to the polish, so it is taken every 4th step
     const bool certify_now = X->prec != 1 || (k % 4) == 0 || k + 1 == P.max_outer;
@@ -1230,14 +1280,14 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* ws, si
   res->marg_viol = cert.viol;
   res->grad_norm = X->gn;
   res->outer_iters = k;
-  res->newton_iters = tot_newton;
-  res->cg_iters = tot_cg;
+  res->newton_iters = ns.newton;
+  res->cg_iters = ns.cg;
   res->sinkhorn_iters = tot_sk;
-  res->armijo_trials = tot_armijo;
+  res->armijo_trials = ns.armijo;
   res->polish_outer = polish_outer;
   res->reanchors = X->reanchors;
   res->status = status;
-  res->max_nnz = max_nnz;
+  res->max_nnz = ns.max_nnz;
   res->dense_passes = X->dense_passes;
   res->kernel_launches = g_launches.load() - launches0;
   X->prof.harvest();

@@ -20,5 +20,6 @@ from .generators import (  # noqa: F401
     sq_euclidean_cost,
     grid_sq_cost,
     square_index_cost,
+    paper_synthetic_problem,
     workload,
 )

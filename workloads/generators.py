@@ -82,6 +82,26 @@ def square_index_cost(m: int, n: int) -> np.ndarray:
     return (i - j) ** 2
 
 
+def paper_synthetic_problem(kind: str, m: int, n: int, seed: int, eta: float = 1e-4,
+                            cost_dtype=np.float64) -> OTProblem:
+    """The paper's synthetic settings (Sec. 5.1): a, b ~ U(0, 1) normalised and
+    C / max with C_ij ~ U(0, 1) ('uniform') or C_ij = (i - j)^2 ('square').
+
+    Draw order: a (m), b (n), then the uniform cost (m*n) for 'uniform'.
+    """
+    rng = np.random.default_rng(seed)
+    a = random_marginal(rng, m, 0.0, 1.0)
+    b = random_marginal(rng, n, 0.0, 1.0)
+    if kind == "uniform":
+        raw = rng.uniform(0.0, 1.0, size=(m, n))
+    elif kind == "square":
+        raw = square_index_cost(m, n)
+    else:
+        raise KeyError(kind)
+    C, scale = _normalised_by_max(raw)
+    return OTProblem(C=C.astype(cost_dtype), a=a, b=b, eta=eta, name=f"{kind}_{m}x{n}_s{seed}", cost_scale=scale)
+
+
 def _normalised_by_max(raw: np.ndarray) -> tuple[np.ndarray, float]:
     mx = float(raw.max())
     scale = 1.0 / mx if mx > 0 else 1.0
