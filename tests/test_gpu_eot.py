@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import ibsn as O  # noqa: E402
-from workloads import paper_synthetic_problem, uniform_points_problem  # noqa: E402
+from workloads import paper_synthetic_problem, sphere_problem, uniform_points_problem  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,7 +35,18 @@ CASES = [
     (lambda: uniform_points_problem(150, 113, seed=71, eta=1e-3), "mixed"),
     (lambda: paper_synthetic_problem("square", 300, 300, seed=72, eta=1e-4), "fp64"),
     (lambda: paper_synthetic_problem("square", 300, 300, seed=72, eta=1e-4), "mixed"),
+    # unbalanced m >> n spherical transport (App. C.4), eta = 1e-3
+    (lambda: sphere_problem(3000, 50, seed=73), "fp64"),
+    (lambda: sphere_problem(3000, 50, seed=73), "mixed"),
 ]
+
+_REF = {}
+
+
+def _oracle(key, prob):
+    if key not in _REF:
+        _REF[key] = O.eibsn(prob.C, prob.a, prob.b, O.IBSNParams(eta=prob.eta))
+    return _REF[key]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
@@ -43,7 +54,7 @@ def test_eot_mode_matches_oracle(case):
     mk, prec = CASES[case]
     prob = mk()
     res = _solve(prob, prec)
-    ref = O.eibsn(prob.C, prob.a, prob.b, O.IBSNParams(eta=prob.eta))
+    ref = _oracle(prob.name, prob)
     assert ref.converged
     assert res["converged"] and res["grad_norm"] < 1e-9, (res["grad_norm"], res["newton_iters"])
     assert res["outer_iters"] == 1

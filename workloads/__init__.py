@@ -21,5 +21,6 @@ from .generators import (  # noqa: F401
     grid_sq_cost,
     square_index_cost,
     paper_synthetic_problem,
+    sphere_problem,
     workload,
 )

@@ -102,6 +102,41 @@ def paper_synthetic_problem(kind: str, m: int, n: int, seed: int, eta: float = 1
     return OTProblem(C=C.astype(cost_dtype), a=a, b=b, eta=eta, name=f"{kind}_{m}x{n}_s{seed}", cost_scale=scale)
 
 
+def _unit_rows(v: np.ndarray) -> np.ndarray:
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def sphere_problem(m: int, n: int, seed: int, eta: float = 1e-3, clusters: int = 24,
+                   cost_dtype=np.float64) -> OTProblem:
+    """Unbalanced spherical transport (the App. C.4 m > n setting, synthetic):
+    demand points x_i on the unit sphere S^2 drawn from `clusters` clustered
+    populations (cluster centres uniform on S^2, Dirichlet(1) cluster weights,
+    angular spread U[0.02, 0.3] rad, Gaussian in the tangent plane), supply
+    points y_j uniform on S^2, C_ij = arccos(<x_i, y_j>) / max, a, b ~ U(0, 1)
+    normalised.  Stands in for the population-density and landmass data,
+    which are not used.
+
+    Draw order: centres (clusters x 3), weights, spreads, labels (m), tangent
+    noise (m x 3), supply directions (n x 3), a (m), b (n).
+    """
+    rng = np.random.default_rng(seed)
+    centres = _unit_rows(rng.standard_normal(size=(clusters, 3)))
+    wts = rng.dirichlet(np.ones(clusters))
+    spread = rng.uniform(0.02, 0.3, size=clusters)
+    labels = rng.choice(clusters, size=m, p=wts)
+    noise = rng.standard_normal(size=(m, 3)) * spread[labels][:, None]
+    c = centres[labels]
+    noise -= (noise * c).sum(axis=1, keepdims=True) * c  # tangent component only
+    x = _unit_rows(c + noise)
+    y = _unit_rows(rng.standard_normal(size=(n, 3)))
+    a = random_marginal(rng, m, 0.0, 1.0)
+    b = random_marginal(rng, n, 0.0, 1.0)
+    raw = np.arccos(np.clip(x @ y.T, -1.0, 1.0))
+    C, scale = _normalised_by_max(raw)
+    return OTProblem(C=C.astype(cost_dtype), a=a, b=b, eta=eta, name=f"sphere_{m}x{n}_s{seed}", x=x, y=y,
+                     cost_scale=scale)
+
+
 def _normalised_by_max(raw: np.ndarray) -> tuple[np.ndarray, float]:
     mx = float(raw.max())
     scale = 1.0 / mx if mx > 0 else 1.0
