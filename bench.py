@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-eta3", dest="eta3", action="store_false",
+                    help="skip the extra mixed solve of the grid workload at eta = 1e-3")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--oracle-job", default="", help=argparse.SUPPRESS)
     ap.add_argument("--max-cg", type=int, default=0, help="CG iteration cap per Newton direction (0: library default)")
@@ -63,7 +65,7 @@ def parse():
     ap.add_argument("--ws-train-n", type=int, default=256, help="warmstart: points per cloud in training")
     ap.add_argument("--ws-eval-n", type=int, default=1024, help="warmstart: points per cloud in evaluation")
     ap.add_argument("--ws-adam-steps", type=int, default=600, help="warmstart: Adam steps")
-    ap.add_argument("--workload", default="grid", choices=["grid", "batch64", "warmstart", "eot", "ablation"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "batch64", "warmstart", "eot", "ablation", "sphere"],
                     help="grid: the 16384-bin headline; batch64: 64 uneven point-cloud problems "
                          "(m, n ~ U{500..5000}) solved by one ibsn_solve_batch call; eot: (E)IBSN on the "
                          "paper's Square EOT setting; ablation: IBSN against IBN (dense Hessian)")
@@ -585,6 +587,54 @@ def run_eot(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sphere(args):
+    """Unbalanced spherical transport (App. C.4, m >> n): (E)IBSN with
+    C = arccos<x, y> / max on synthetic clustered demand and uniform supply
+    points on S^2, eta = 1e-3, to ||g|| < 1e-9, for n in {50, 80} and growing
+    m, in float64 and mixed precision.  One step = the largest m, n = 80, mixed."""
+    import torch
+
+    import paper_2603_07156_gb300 as G
+    from workloads import sphere_problem
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sizes = [int(v) for v in args.sizes.split(",")] if args.sizes else [10_000, 100_000, 1_000_000]
+    rows = []
+    for m in sizes:
+        for n in (50, 80):
+            prob = sphere_problem(m, n, seed=0)
+            gp = _dense_problem(G, prob, dev)
+            for prec in ("fp64", "mixed"):
+                r = _timed_solve(G, gp, G.params(precision=prec, eot=1, profile=1, max_newton=200), dev, stream)
+                rows.append({"m": m, "n": n, "precision": prec, "s": r["s"], "cg_s": r["cg_s"],
+                             "newton": r["newton_iters"], "mean_cg": r["cg_iters"] / max(r["newton_iters"], 1),
+                             "sinkhorn": r["sinkhorn_iters"], "grad_norm": r["grad_norm"],
+                             "converged": r["converged"]})
+            del gp
+    m, n = sizes[-1], 80
+    prob = sphere_problem(m, n, seed=0)
+    gp = _dense_problem(G, prob, dev)
+    prm = G.params(precision="mixed", eot=1, max_newton=200)
+    for _ in range(args.warmup):
+        _timed_solve(G, gp, prm, dev, stream)
+    times = [_timed_solve(G, gp, prm, dev, stream)["s"] for _ in range(args.steps)]
+    rep = replica_line_fields(statistics.mean(times), world)
+    if rank != 0:
+        return
+    line = {"metric": f"s to ||g|| < 1e-9 on one EOT subproblem ((E)IBSN), spherical cost m={m}, n={n}",
+            "value": rep["value"], "unit": "s", "n_gpus": rep["n_gpus"], "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rep["value"] * 1e3, "higher_is_better": False,
+            "scaling": rep["scaling"], "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "clustered demand / uniform supply points on S^2, C = arccos<x,y>/max, "
+                                   "U(0,1) marginals, seed 0, eta=1e-3, X = 1 1^T", "m": m, "n": n,
+                       "precision": "mixed", "parallelism": f"replicas x{world}"},
+            "table": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_ablation(args):
     """IBSN against IBN (no Hessian sparsification) on the paper's synthetic
     Uniform and Square settings (App. C.3, Table 1): eta = 1e-4, at most 300
@@ -659,6 +709,9 @@ def main():
     if args.workload == "ablation":
         run_ablation(args)
         return
+    if args.workload == "sphere":
+        run_sphere(args)
+        return
     import numpy as np
     import torch
 
@@ -718,7 +771,7 @@ def main():
         b_h = torch.tensor(b_np, dtype=torch.float64).pin_memory()
         g_h = torch.empty(n, dtype=torch.float64).pin_memory()
         e_times = []
-        for _ in range(args.steps):
+        for _ in range(min(args.steps, 5)):
             torch.cuda.synchronize(dev)
             ev0.record(stream)
             a_d = a_h.to(dev, non_blocking=True)
@@ -742,8 +795,31 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         t64 = ev0.elapsed_time(ev1) / 1e3
+        r_mx = results[-1]
         fp64 = {"s": t64, "rel_gap": r64["rel_gap"], "outer_iters": r64["outer_iters"],
-                "converged": r64["converged"], "primal": r64["primal"], "speedup": t64 / t_mean}
+                "converged": r64["converged"], "primal": r64["primal"], "speedup": t64 / t_mean,
+                # accuracy of the mixed result against the float64 path (both certified)
+                "mixed_primal_rel_diff": abs(r_mx["primal"] - r64["primal"]) / abs(r64["primal"]),
+                "mixed_dual_rel_diff": abs(r_mx["dual"] - r64["dual"]) / abs(r64["dual"])}
+
+    # the image-setting eta = 1e-3 of the paper (Sec. 5.2) on the same workload: one mixed solve
+    eta3 = None
+    if args.eta3 and rank == 0 and args.precision == "mixed":
+        prob3 = G.Problem(a=a, b=b, eta=1e-3, grid=(h, h), cost_scale=scale)
+        ev0.record(stream)
+        r3 = G.solve(prob3, G.params(precision="mixed", **extra), workspace=ws)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        eta3 = {"eta": 1e-3, "s": ev0.elapsed_time(ev1) / 1e3, "rel_gap": r3["rel_gap"],
+                "outer_iters": r3["outer_iters"], "newton_iters": r3["newton_iters"], "cg_iters": r3["cg_iters"],
+                "primal": r3["primal"], "converged": r3["converged"]}
+        try:
+            rec = json.load(open(TRAJECTORY)).get(f"{h}:0.001", {})
+            if "fp64_s" in rec:
+                eta3["fp64_plain_recorded_s"] = rec["fp64_s"]
+                eta3["speedup_vs_recorded_fp64"] = rec["fp64_s"] / eta3["s"]
+        except Exception:
+            pass
 
     if rank != 0:
         return
@@ -780,7 +856,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_mean * 1e3, "higher_is_better": False, "scaling": rep["scaling"],
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": grid_config(args, world),
-        "roofline": roof, "plan_pass": plan_pass, "fp64_plain": fp64,
+        "roofline": roof, "plan_pass": plan_pass, "fp64_plain": fp64, "eta_1e-3": eta3,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "solve": {k: r0[k] for k in ("rel_gap", "primal", "dual", "outer_iters", "newton_iters", "cg_iters",
                                      "sinkhorn_iters", "polish_outer", "max_nnz", "dense_passes",

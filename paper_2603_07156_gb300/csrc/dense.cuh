@@ -68,6 +68,7 @@ struct DenseArgs {
   const float* wvl;
   float lamh, laml;
   double* scal;            // slot S_DEVERR records a timed-out wait
+  int stages;              // float row stream: row buffers in flight (1 or 2; 0 reads as 1)
   // float-float passes: per-row results for the row kernels, a_i - fl32(a_i)
   double* rowS0;
   double* rowS1;
@@ -260,50 +261,69 @@ __device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) 
   }
 }
 
+constexpr int kMaxRowStages = 2;
+
 template <typename T>
 struct RowStream {
   float* buf = nullptr;
-  uint32_t bar = 0;
-  uint32_t parity = 0;
+  uint32_t bar0 = 0;       // shared address of the first stage's mbarrier (8 bytes apart)
+  uint32_t parity = 0;     // bit s: phase parity stage s waits for next
+  int ns = 1;              // stages: row copies kept in flight
+  int base = 0;            // first row of the block
 
-  __device__ __forceinline__ void issue(const DenseArgs<T>& A, int row) {  // one thread
+  __device__ __forceinline__ void issue(const DenseArgs<T>& A, int row, int stage) {  // one thread
     const uint32_t bytes = (uint32_t)(A.ldk * (int64_t)sizeof(float));
     const float* src = reinterpret_cast<const float*>(A.K) + (int64_t)row * A.ldk;
-    // the block's reads of the previous row (generic proxy) precede this write (async proxy)
+    const uint32_t bar = bar0 + 8u * (uint32_t)stage;
+    // the block's reads of this stage's previous row (generic proxy) precede this write (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(buf)), "l"(src), "r"(bytes), "r"(bar)
+                 ::"r"(smem_u32(buf + (int64_t)stage * A.ldk)), "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
   }
 
-  // set up the barrier and start the copy of the block's first row
+  // set up the barriers and start the copies of the block's first rows;
+  // mbar points to kMaxRowStages barriers, the dynamic shared memory holds
+  // A.stages row buffers of ldk floats
   __device__ __forceinline__ void start(const DenseArgs<T>& A, double* dyn, unsigned long long* mbar, int r0, int r1) {
     if constexpr (std::is_same<T, float>::value) {
       buf = reinterpret_cast<float*>(dyn);
-      bar = smem_u32(mbar);
+      bar0 = smem_u32(mbar);
+      ns = A.stages > 1 ? kMaxRowStages : 1;
+      base = r0;
       if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        for (int q = 0; q < ns; ++q)
+          asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * (uint32_t)q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (r0 < r1) issue(A, r0);
+        for (int q = 0; q < ns && r0 + q < r1; ++q) issue(A, r0 + q, q);
       }
       __syncthreads();
     }
   }
 
-  // row i into the tile; starts the copy of row i+1.  False: a wait ran out
-  // (recorded), every thread of the block returns false together.
+  // row i into the tile; starts the copy of row i + ns into the freed stage.
+  // False: a wait ran out (recorded); thread 0 then waits, again bounded, for
+  // the block's other copy in flight, and every thread returns false together.
   template <int TG, int CH>
   __device__ __forceinline__ bool row(Tile<T, TG, CH>& t, const DenseArgs<T>& A, int i, int r1) {
     if constexpr (std::is_same<T, float>::value) {
-      const bool ok = mbar_wait_parity(bar, parity);
-      parity ^= 1u;
-      if (ok) t.load_smem(buf, A.dv, A.ldk);
+      const int q = (i - base) & (ns - 1);
+      const bool ok = mbar_wait_parity(bar0 + 8u * (uint32_t)q, (parity >> q) & 1u);
+      parity ^= 1u << q;
+      if (ok) t.load_smem(buf + (int64_t)q * A.ldk, A.dv, A.ldk);
       if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0 && A.scal != nullptr) A.scal[S_DEVERR] = 1.0;
+        if (threadIdx.x == 0) {
+          if (A.scal != nullptr) A.scal[S_DEVERR] = 1.0;
+          if (ns > 1 && i + 1 < r1) {
+            const int q2 = (i + 1 - base) & (ns - 1);
+            mbar_wait_parity(bar0 + 8u * (uint32_t)q2, (parity >> q2) & 1u);
+          }
+        }
+        __syncthreads();
         return false;
       }
-      if (threadIdx.x == 0 && i + 1 < r1) issue(A, i + 1);
+      if (threadIdx.x == 0 && i + ns < r1) issue(A, i + ns, q);
     } else {
       t.load(A.K + (int64_t)i * A.ldk, A.dv, A.ldk);
     }
@@ -344,7 +364,7 @@ __device__ __forceinline__ void row_sum(T (&v)[K], float* shf) {
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
@@ -353,7 +373,7 @@ __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<T> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   T lpart = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(TG) k_plan(DenseArgs<T> A) {
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
@@ -396,7 +416,7 @@ __global__ void __launch_bounds__(TG) k_armijo(DenseArgs<T> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<T> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   T ppsi = T(0), plog = T(0);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
@@ -490,7 +510,7 @@ struct StopTau<double> {
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
@@ -498,7 +518,7 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<T> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   const double S_ec = A.scal[S_ECSUM];  // ||e_c||_1, formed on the device with the gradient
   const T invS = (T)(S_ec > 0.0 ? 1.0 / S_ec : 0.0);
   T dpart = T(0);
@@ -575,7 +595,7 @@ __global__ void __launch_bounds__(TG) k_stop(DenseArgs<T> A) {
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   __shared__ int shi[TG / 32];
@@ -589,7 +609,7 @@ __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<T> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   const T rho = (T)A.s1;
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
@@ -697,7 +717,7 @@ __device__ __forceinline__ double cost_at(const CostRef& c, int i, int64_t j) {
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ double shd[6 * (TG / 32)];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
@@ -707,7 +727,7 @@ __global__ void __launch_bounds__(TG) k_certify(DenseArgs<T> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<T> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   double part[7] = {0, 0, 0, 0, 0, 0, 0};
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
@@ -843,14 +863,14 @@ __global__ void __launch_bounds__(TG) k_reanchor(DenseArgs<T> A) {
 template <typename T, int TG, int CH>
 __global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ T sht[TG / 32];
   constexpr int V = VecT<T>::N;
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<T> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   Tile<T, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
@@ -1059,7 +1079,7 @@ __device__ __forceinline__ FF ff_of(double v) {
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
@@ -1069,7 +1089,7 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<float> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
@@ -1114,7 +1134,7 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;
@@ -1124,7 +1144,7 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<float> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   // an entry can grow by exp(t max|Delta|/eta) at the trial point: keep more
   const float keep = kFFKeep * (float)A.s2;
   Tile<float, TG, CH> t;
@@ -1180,7 +1200,7 @@ template <int TG, int CH, int KIND>
 __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   const CostRef cost = kind_ref<KIND>(A.cost);  // the kind is a compile-time constant below
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   __shared__ long long shl[TG / 32];
@@ -1196,7 +1216,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<float> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
@@ -1316,7 +1336,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
 template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
   extern __shared__ __align__(128) double dyn_sm[];
-  __shared__ unsigned long long s_mbar;
+  __shared__ unsigned long long s_mbar[kMaxRowStages];
   __shared__ double shd[2 * (TG / 32)];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
@@ -1324,7 +1344,7 @@ __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
   int r0, r1;
   row_range(A.m, A.rows_per_block, r0, r1);
   RowStream<float> rs;
-  rs.start(A, dyn_sm, &s_mbar, r0, r1);
+  rs.start(A, dyn_sm, s_mbar, r0, r1);
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;

@@ -43,6 +43,10 @@ struct TileTable<double> {
   static constexpr int ch[count] = {2, 4, 4, 8, 8, 8};
 };
 
+// Shared memory up to which a float pass keeps two row buffers (a 16384-wide
+// float row is 64 KiB; two leave room on the SM for the L1 cache).
+constexpr size_t kTwoStageSmemMax = 160 * 1024;
+
 template <typename T>
 static int pick_tile(int64_t n) {
   for (int q = 0; q < TileTable<T>::count; ++q)
@@ -81,7 +85,9 @@ cudaError_t launch_dense_t(Pass p, DenseArgs<T>& A, int nsm, cudaStream_t st, Pa
   if (std::is_same<T, double>::value) {
     if (pass_uses_colacc(p)) smem = (size_t)A.ldk * sizeof(double);
   } else if (p != Pass::Reanchor) {
-    smem = (size_t)A.ldk * sizeof(float);
+    // two row copies in flight per block when both buffers fit comfortably
+    A.stages = 2 * (size_t)A.ldk * sizeof(float) <= kTwoStageSmemMax ? 2 : 1;
+    smem = (size_t)A.stages * (size_t)A.ldk * sizeof(float);
   }
   // one-time opt-in to large dynamic shared memory, and cached occupancy
   static std::mutex mu;
@@ -164,6 +170,7 @@ static const void* ff_kernel_for(int q, Pass p, int kind) {
 }
 
 inline cudaError_t launch_dense_ff_t(Pass p, DenseArgs<float>& A, int nsm, cudaStream_t st, PassGeom* geom) {
+  A.stages = 1;  // the float64 column accumulator follows the single row buffer
   const int q = pick_tile<float>(A.n);
   if (q < 0) return cudaErrorInvalidValue;
   const void* fn = ff_kernel_for(q, p, A.cost.kind);
