@@ -50,9 +50,14 @@ typedef enum ibsn_status {
 typedef enum ibsn_cost_kind {
   IBSN_COST_DENSE_F64 = 0,   /* C given as a dense row-major float64 matrix */
   IBSN_COST_DENSE_F32 = 1,   /* C given as a dense row-major float32 matrix (exact values) */
-  IBSN_COST_GRID2D = 2       /* bins of one h x w grid (row-major), m = n = h*w:
+  IBSN_COST_GRID2D = 2,      /* bins of one h x w grid (row-major), m = n = h*w:
                                 C_ij = cost_scale * ((r_i - r_j)^2 + (c_i - c_j)^2),
                                 rebuilt on the fly from the integer coordinates */
+  IBSN_COST_SQEUCLID_POINTS = 3  /* point clouds x (m x dim) and y (n x dim), float64
+                                row-major device arrays, 1 <= dim <= 16:
+                                C_ij = cost_scale * ||x_i - y_j||^2, rebuilt on the fly
+                                (in float-float arithmetic, ~2^-46 relative) wherever
+                                the solver reads C; no m x n cost matrix is stored */
 } ibsn_cost_kind;
 
 typedef enum ibsn_precision {
@@ -70,10 +75,13 @@ typedef struct ibsn_problem {
   const double* a;           /* m, source marginal */
   const double* b;           /* n, target marginal */
   double eta;                /* proximal weight eta > 0 (Eq. 2) */
-  double cost_scale;         /* GRID2D: C = cost_scale * integer squared distance */
+  double cost_scale;         /* GRID2D: C = cost_scale * integer squared distance;
+                                SQEUCLID_POINTS: C = cost_scale * squared distance */
   int32_t cost_kind;         /* ibsn_cost_kind */
   int32_t grid_h, grid_w;    /* GRID2D */
-  int32_t reserved_;
+  int32_t dim;               /* SQEUCLID_POINTS: coordinates per point */
+  const double* x;           /* SQEUCLID_POINTS: m x dim source points (device) */
+  const double* y;           /* SQEUCLID_POINTS: n x dim target points (device) */
 } ibsn_problem;
 
 /* Parameters.  ibsn_params_default() fills the paper's constants. */

@@ -22,7 +22,8 @@ class IbsnProblem(C.Structure):
         ("m", C.c_int64), ("n", C.c_int64), ("ldc", C.c_int64),
         ("C", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p),
         ("eta", C.c_double), ("cost_scale", C.c_double),
-        ("cost_kind", C.c_int32), ("grid_h", C.c_int32), ("grid_w", C.c_int32), ("reserved_", C.c_int32),
+        ("cost_kind", C.c_int32), ("grid_h", C.c_int32), ("grid_w", C.c_int32), ("dim", C.c_int32),
+        ("x", C.c_void_p), ("y", C.c_void_p),
     ]
 
 

@@ -15,7 +15,7 @@ import torch
 
 from . import _native as N
 
-COST_DENSE_F64, COST_DENSE_F32, COST_GRID2D = 0, 1, 2
+COST_DENSE_F64, COST_DENSE_F32, COST_GRID2D, COST_SQEUCLID_POINTS = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 _PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED, "ff": 2, PREC_FP64: PREC_FP64, PREC_MIXED: PREC_MIXED, 2: 2}
 
@@ -56,12 +56,21 @@ class Problem:
     C: torch.Tensor | None = None
     grid: tuple[int, int] | None = None
     cost_scale: float = 1.0
+    x: torch.Tensor | None = None  # point cost: (m, dim) float64 source points
+    y: torch.Tensor | None = None  # point cost: (n, dim) float64 target points
 
     def __post_init__(self):
         for name in ("a", "b"):
             t = getattr(self, name)
             if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
                 raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+        if self.x is not None or self.y is not None:
+            for name in ("x", "y"):
+                t = getattr(self, name)
+                if t is None or t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2 or not t.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous 2-D float64 CUDA tensor")
+            if self.x.shape[1] != self.y.shape[1]:
+                raise ValueError("x and y must have the same number of coordinates")
         if self.C is not None:
             if self.C.dtype not in (torch.float64, torch.float32) or not self.C.is_cuda or self.C.dim() != 2:
                 raise ValueError("C must be a 2-D float32/float64 CUDA tensor")
@@ -73,7 +82,13 @@ class Problem:
         s.m, s.n = int(self.a.numel()), int(self.b.numel())
         s.a, s.b = _ptr(self.a), _ptr(self.b)
         s.eta = float(self.eta)
-        if self.grid is not None:
+        if self.x is not None:
+            s.cost_kind = COST_SQEUCLID_POINTS
+            s.x, s.y = _ptr(self.x), _ptr(self.y)
+            s.dim = int(self.x.shape[1])
+            s.cost_scale = float(self.cost_scale)
+            s.ldc = s.n
+        elif self.grid is not None:
             s.cost_kind = COST_GRID2D
             s.grid_h, s.grid_w = int(self.grid[0]), int(self.grid[1])
             s.cost_scale = float(self.cost_scale)

@@ -693,6 +693,16 @@ __global__ void __launch_bounds__(TG) k_sparsify(DenseArgs<T> A) {
 __device__ __forceinline__ double cost_at(const CostRef& c, int i, int64_t j) {
   if (c.kind == 0) return __ldg(static_cast<const double*>(c.C) + (int64_t)i * c.ldc + j);
   if (c.kind == 1) return (double)__ldg(static_cast<const float*>(c.C) + (int64_t)i * c.ldc + j);
+  if (c.kind == 3) {
+    const double* xi = c.px + (int64_t)i * c.dim;
+    const double* yj = c.py + j * c.dim;
+    double q = 0.0;
+    for (int k = 0; k < c.dim; ++k) {
+      const double t = __ldg(xi + k) - __ldg(yj + k);
+      q = fma(t, t, q);
+    }
+    return c.scale * q;
+  }
   int ri, ci, rj, cj;
   if (c.rc != nullptr) {
     const int pi = __ldg(c.rc + i), pj = __ldg(c.rc + j);
@@ -914,6 +924,26 @@ struct FFRow {
 // float and scale split as sh + sl).
 __device__ __forceinline__ float2 cost_ff(const CostRef& c, int i, int64_t j, float sh, float sl) {
   if (c.kind == 1) return make_float2(__ldg(static_cast<const float*>(c.C) + (int64_t)i * c.ldc + j), 0.f);
+  if (c.kind == 3) {
+    // sum_k (x_ik - y_jk)^2 in float-float from the (hi, lo) coordinates:
+    // each difference exactly as TwoSum(xh, -yh) + (xl - yl), its square by
+    // TwoProduct, the sum and the final scale in float-float
+    const float2* xi = c.xs + (int64_t)i * c.dim;
+    const float2* yj = c.ys + j * c.dim;
+    FF q{0.f, 0.f};
+    for (int k = 0; k < c.dim; ++k) {
+      const float2 xv = __ldg(xi + k), yv = __ldg(yj + k);
+      const float dh = xv.x - yv.x;
+      const float bv = dh - xv.x;
+      const float err = (xv.x - (dh - bv)) + (-yv.x - bv);
+      const FF d = ff_add(FF{dh, 0.f}, FF{err + (xv.y - yv.y), 0.f});
+      const float p = d.hi * d.hi;
+      const float pl = fmaf(d.hi, d.hi, -p) + 2.f * d.hi * d.lo;
+      q = ff_add(q, FF{p, pl});
+    }
+    const float r = q.hi * sh;
+    return make_float2(r, fmaf(q.hi, sh, -r) + fmaf(q.hi, sl, q.lo * sh));
+  }
   if (c.kind == 0) {
     const double C = __ldg(static_cast<const double*>(c.C) + (int64_t)i * c.ldc + j);
     const float h = (float)C;

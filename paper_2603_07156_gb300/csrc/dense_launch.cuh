@@ -152,6 +152,7 @@ static const void* ff_kernel(Pass p, int kind) {
     default:
       if (kind == 0) return ff_kernel_k<TG, CH, 0>(p);
       if (kind == 1) return ff_kernel_k<TG, CH, 1>(p);
+      if (kind == 3) return ff_kernel_k<TG, CH, 3>(p);
       return ff_kernel_k<TG, CH, 2>(p);
   }
 }
@@ -180,9 +181,9 @@ inline cudaError_t launch_dense_ff_t(Pass p, DenseArgs<float>& A, int nsm, cudaS
   const size_t smem = p == Pass::Reanchor ? 0
                       : (size_t)A.ldk * sizeof(float) + (p == Pass::Export ? 0 : (size_t)A.ldk * sizeof(double));
   static std::mutex mu;
-  const int kk = (A.cost.kind >= 0 && A.cost.kind <= 2) ? A.cost.kind : 2;
-  static int occ_cache[TileTable<float>::count][(int)Pass::kCount][3] = {};
-  static size_t smem_set[TileTable<float>::count][(int)Pass::kCount][3] = {};
+  const int kk = (A.cost.kind >= 0 && A.cost.kind <= 3) ? A.cost.kind : 2;
+  static int occ_cache[TileTable<float>::count][(int)Pass::kCount][4] = {};
+  static size_t smem_set[TileTable<float>::count][(int)Pass::kCount][4] = {};
   int occ;
   {
     std::lock_guard<std::mutex> lk(mu);

@@ -21,9 +21,19 @@ struct CostRef {
   int64_t ldc;
   int kind;      // ibsn_cost_kind
   int gw;        // grid width (GRID2D)
-  double scale;  // GRID2D scale
+  double scale;  // GRID2D / SQEUCLID_POINTS scale
   const int* rc; // GRID2D: bin coordinates packed as row | col << 16 (n entries), or null
+  // SQEUCLID_POINTS: C_ij = scale * ||x_i - y_j||^2 with x (m x dim) and y (n x dim)
+  // row-major float64; xs / ys hold every coordinate as a float pair (hi, lo)
+  // with hi + lo = the float64 value to 2^-48 (null: not set up)
+  const double* px;
+  const double* py;
+  const float2* xs;
+  const float2* ys;
+  int dim;
 };
+
+constexpr int kMaxPointDim = 16;    // coordinates per point of the on-the-fly point cost
 
 enum class Pass : int { Plan = 0, Armijo, Stop, Sparsify, Certify, Reanchor, Export, kCount };
 
@@ -136,7 +146,9 @@ cudaError_t launch_certify_cols(int64_t n, const double* b, const double* colF, 
                                 double ersum, double* scal, const RedBuf& rb, cudaStream_t st);
 cudaError_t launch_validate_marginals(int64_t m, int64_t n, const double* a, const double* b, double* scal,
                                       cudaStream_t st);
-cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal,
+cudaError_t launch_split_coords(int64_t count, const double* x, float2* out, cudaStream_t st);
+cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, const double* px,
+                                 const double* py, int dim, double scale, double* scal,
                                  cudaStream_t st);
 cudaError_t launch_certify_prep(int64_t n, const double* gam, float* gam32, float* gamlo, double* scal,
                                 const RedBuf& rb, cudaStream_t st);

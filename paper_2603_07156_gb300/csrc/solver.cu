@@ -161,6 +161,7 @@ struct ibsn_ctx {
   double *rowS0, *rowS1, *rowM;  // per-row results of the float-float passes
   double* rowbuf;                // 6 x m per-row results of the float-float certificate
   int* gridrc;                   // grid cost: bin coordinates per column (null otherwise)
+  float2 *xs, *ys;               // point cost: coordinates as float pairs (null otherwise)
   float* alo32;                  // a - fl32(a)
   float *d32, *em32, *a32, *gam32, *wvh, *wvl;
   float *dlo32, *emlo32, *gamlo32;  // float-float lo parts
@@ -216,6 +217,11 @@ int check_problem(const ibsn_problem* pr) {
         return IBSN_ERR_INVALID_ARG;
       if (!(pr->cost_scale >= 0.0) || !std::isfinite(pr->cost_scale)) return IBSN_ERR_NONFINITE;
       break;
+    case IBSN_COST_SQEUCLID_POINTS:
+      if (!pr->x || !pr->y || pr->dim < 1) return IBSN_ERR_INVALID_ARG;
+      if (pr->dim > kMaxPointDim) return IBSN_ERR_UNSUPPORTED;
+      if (!(pr->cost_scale >= 0.0) || !std::isfinite(pr->cost_scale)) return IBSN_ERR_NONFINITE;
+      break;
     default:
       return IBSN_ERR_INVALID_ARG;
   }
@@ -243,6 +249,9 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   X->alo32 = cv.take<float>(m);
   X->rowbuf = cv.take<double>(6 * (size_t)m);
   X->gridrc = pr->cost_kind == IBSN_COST_GRID2D ? cv.take<int>(n) : nullptr;
+  const bool pts = pr->cost_kind == IBSN_COST_SQEUCLID_POINTS;
+  X->xs = pts ? cv.take<float2>((size_t)m * pr->dim) : nullptr;
+  X->ys = pts ? cv.take<float2>((size_t)n * pr->dim) : nullptr;
   float** fvec[] = {&X->d32,      &X->em32,      &X->gam32,      &X->rv.y32,   &X->rv.om32, &X->rv.ec32,
                     &X->rv.ecs32, &X->rv.ecsl32, &X->rv.lec32, &X->wvh,      &X->wvl, &X->rv.hom32,
                     &X->dlo32,    &X->emlo32,    &X->gamlo32,    &X->rv.ylo32, &X->rv.omlo32};
@@ -438,6 +447,7 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
 // algorithmic bytes of one dense pass (see ibsn_result.pass_bytes)
 double pass_bytes(ibsn_ctx* X, Pass p, Mode md) {
   const double mn = (double)X->m * (double)X->n;
+  // bytes of C read per entry: dense kinds only (grid and point costs are rebuilt on the fly)
   const double sc = X->cost.kind == 0 ? 8.0 : (X->cost.kind == 1 ? 4.0 : 0.0);
   const double sk = md == Mode::F64 ? 8.0 : 4.0;
   switch (p) {
@@ -823,6 +833,11 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   X->cost.gw = pr->grid_w;
   X->cost.scale = pr->cost_scale;
   X->cost.rc = X->gridrc;
+  X->cost.px = pr->x;
+  X->cost.py = pr->y;
+  X->cost.xs = X->xs;
+  X->cost.ys = X->ys;
+  X->cost.dim = pr->cost_kind == IBSN_COST_SQEUCLID_POINTS ? pr->dim : 0;
   X->a = pr->a;
   X->b = pr->b;
   X->eta = pr->eta;
@@ -845,7 +860,12 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   // validation (Eq. 1): a, b > 0, finite, sums 1; C finite and >= 0
   if (launch_validate_marginals(pr->m, pr->n, pr->a, pr->b, X->scal, st) != cudaSuccess) return fail(IBSN_ERR_CUDA);
   if (pr->cost_kind != IBSN_COST_GRID2D &&
-      launch_validate_cost(pr->m, pr->n, pr->C, pr->ldc, pr->cost_kind, X->scal, st) != cudaSuccess)
+      launch_validate_cost(pr->m, pr->n, pr->C, pr->ldc, pr->cost_kind, pr->x, pr->y, X->cost.dim, pr->cost_scale,
+                           X->scal, st) != cudaSuccess)
+    return fail(IBSN_ERR_CUDA);
+  if (pr->cost_kind == IBSN_COST_SQEUCLID_POINTS &&
+      (launch_split_coords(pr->m * pr->dim, pr->x, X->xs, st) != cudaSuccess ||
+       launch_split_coords(pr->n * pr->dim, pr->y, X->ys, st) != cudaSuccess))
     return fail(IBSN_ERR_CUDA);
   if (pr->cost_kind == IBSN_COST_GRID2D) {
     // max C of the grid cost (two opposite corners) and sum C^2 over all pairs

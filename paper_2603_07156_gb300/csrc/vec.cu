@@ -434,14 +434,24 @@ __global__ void __launch_bounds__(kVB) k_validate_marginals(int64_t m, int64_t n
   }
 }
 
-__global__ void k_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal) {
+__global__ void k_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, const double* px,
+                                const double* py, int dim, double scale, double* scal) {
   unsigned int bad = 0;
   double cmax = 0.0, c2 = 0.0;
   const int64_t total = m * n;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / n, j = q - i * n;
-    const double v = kind == 0 ? static_cast<const double*>(C)[i * ldc + j]
-                               : (double)static_cast<const float*>(C)[i * ldc + j];
+    double v;
+    if (kind == 3) {  // points: C_ij = scale ||x_i - y_j||^2 (non-finite coordinates give NaN)
+      double s = 0.0;
+      for (int k = 0; k < dim; ++k) {
+        const double t = px[i * dim + k] - py[j * dim + k];
+        s = fma(t, t, s);
+      }
+      v = scale * s;
+    } else {
+      v = kind == 0 ? static_cast<const double*>(C)[i * ldc + j] : (double)static_cast<const float*>(C)[i * ldc + j];
+    }
     if (!(v >= 0.0) || !isfinite(v)) ++bad;
     else { cmax = fmax(cmax, v); c2 += v * v; }
   }
@@ -572,7 +582,23 @@ cudaError_t launch_validate_marginals(int64_t m, int64_t n, const double* a, con
   note_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, double* scal,
+// coordinates as float pairs (hi, lo) with hi + lo = x to 2^-48 relative
+__global__ void k_split_coords(int64_t count, const double* __restrict__ x, float2* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < count) {
+    const double v = x[q];
+    const float h = (float)v;
+    out[q] = make_float2(h, (float)(v - (double)h));
+  }
+}
+cudaError_t launch_split_coords(int64_t count, const double* x, float2* out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_split_coords<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, x, out);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, const double* px,
+                                 const double* py, int dim, double scale, double* scal,
                                  cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(&scal[S_CBAD], 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
@@ -581,7 +607,7 @@ cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ld
   e = cudaMemsetAsync(&scal[S_C2SUM], 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
   if (kind != 0 && kind != 1) return cudaSuccess;
-  k_validate_cost<<<1216, 256, 0, st>>>(m, n, C, ldc, kind, scal);
+  k_validate_cost<<<1216, 256, 0, st>>>(m, n, C, ldc, kind, px, py, dim, scale, scal);
   note_launch();
   return cudaGetLastError();
 }
