@@ -446,12 +446,19 @@ def run_warmstart(args):
     torch.cuda.set_device(dev)
     prm = G.params(precision="mixed")
 
-    def gpu(p):
+    from types import SimpleNamespace
+
+    def gpu(p):  # squared-Euclidean cost rebuilt on the fly from the points
         t = lambda v: torch.tensor(v, dtype=torch.float64, device=dev)  # noqa: E731
-        return G.Problem(a=t(p.a), b=t(p.b), eta=p.eta, C=t(p.C).to(torch.float32).contiguous())
+        return G.Problem(a=t(p.a), b=t(p.b), eta=p.eta, x=t(p.x).contiguous(), y=t(p.y).contiguous(),
+                         cost_scale=p.cost_scale)
+
+    def clouds(n, seed):  # the generator's points and marginals, without its cost matrix
+        p = warmstart_gmm_problem(n, seed)
+        return SimpleNamespace(x=p.x, y=p.y, a=p.a, b=p.b, eta=p.eta, cost_scale=p.cost_scale)
 
     t0 = time.perf_counter()
-    train = [warmstart_gmm_problem(args.ws_train_n, 10_000 + s) for s in range(args.ws_train)]
+    train = [clouds(args.ws_train_n, 10_000 + s) for s in range(args.ws_train)]
     targets, solved = [], 0
     for k in range(0, len(train), 32):  # training solves run concurrently, 32 problems per batched call
         outs = G.solve_batch([gpu(p) for p in train[k:k + 32]], prm, threads=args.batch_threads)
@@ -470,7 +477,7 @@ def run_warmstart(args):
     t_train = time.perf_counter() - t0
 
     def evaluate(seed):
-        p = warmstart_gmm_problem(args.ws_eval_n, 20_000 + seed)
+        p = clouds(args.ws_eval_n, 20_000 + seed)
         gp = gpu(p)
         ws = G.alloc_workspace(gp, prm)
         torch.cuda.synchronize(dev)

@@ -47,6 +47,15 @@ struct TileTable<double> {
 // float row is 64 KiB; two leave room on the SM for the L1 cache).
 constexpr size_t kTwoStageSmemMax = 160 * 1024;
 
+// The stop-test pass holds no column accumulators, so its float tiles take
+// twice the threads (half the chunks per thread) from the third configuration
+// on: same row capacity, twice the warps to hide its latency.
+struct StopTileTable {
+  static constexpr int count = 6;
+  static constexpr int tg[count] = {64, 128, 256, 512, 512, 1024};
+  static constexpr int ch[count] = {1, 2, 2, 2, 4, 4};
+};
+
 template <typename T>
 static int pick_tile(int64_t n) {
   for (int q = 0; q < TileTable<T>::count; ++q)
@@ -56,6 +65,18 @@ static int pick_tile(int64_t n) {
 
 template <typename T>
 static const void* kernel_for(int q, Pass p) {
+  if (std::is_same<T, float>::value && p == Pass::Stop) {
+    using ST = StopTileTable;
+    switch (q) {
+      case 0: return (const void*)k_stop<T, ST::tg[0], ST::ch[0]>;
+      case 1: return (const void*)k_stop<T, ST::tg[1], ST::ch[1]>;
+      case 2: return (const void*)k_stop<T, ST::tg[2], ST::ch[2]>;
+      case 3: return (const void*)k_stop<T, ST::tg[3], ST::ch[3]>;
+      case 4: return (const void*)k_stop<T, ST::tg[4], ST::ch[4]>;
+      case 5: return (const void*)k_stop<T, ST::tg[5], ST::ch[5]>;
+      default: return nullptr;
+    }
+  }
   switch (q) {
     case 0: return dense_kernel<T, TileTable<T>::tg[0], TileTable<T>::ch[0]>(p);
     case 1: return dense_kernel<T, TileTable<T>::tg[1], TileTable<T>::ch[1]>(p);
@@ -79,7 +100,8 @@ cudaError_t launch_dense_t(Pass p, DenseArgs<T>& A, int nsm, cudaStream_t st, Pa
   const int q = pick_tile<T>(A.n);
   if (q < 0) return cudaErrorInvalidValue;
   const void* fn = kernel_for<T>(q, p);
-  const int tg = TileTable<T>::tg[q];
+  const bool stop_tile = std::is_same<T, float>::value && p == Pass::Stop;
+  const int tg = stop_tile ? StopTileTable::tg[q] : TileTable<T>::tg[q];
   // float64 passes: column accumulator; float passes: the row buffer of the row stream
   size_t smem = 0;
   if (std::is_same<T, double>::value) {
@@ -123,7 +145,7 @@ cudaError_t launch_dense_t(Pass p, DenseArgs<T>& A, int nsm, cudaStream_t st, Pa
   note_launch();
   if (geom) {
     geom->tg = tg;
-    geom->ch = TileTable<T>::ch[q];
+    geom->ch = stop_tile ? StopTileTable::ch[q] : TileTable<T>::ch[q];
     geom->nb = nb;
     geom->rpb = rpb;
     geom->smem = smem;

@@ -158,6 +158,8 @@ def solve_warm(problem: Problem, prm: N.IbsnParams, gamma_hat: torch.Tensor, wor
     """Judge gamma_hat against the fallback start (zero, or the given
     potential), then solve from the winner.  The result carries warm_used
     and the judge's objectives and gradient norms."""
+    if fallback is None and prm.gamma0:
+        raise ValueError("prm.gamma0 is set: pass that start as `fallback` so that the judge compares with it")
     ws = workspace if workspace is not None else alloc_workspace(problem, prm)
     j = judge(problem, prm, gamma_hat, ws, fallback=fallback)
     p2 = N.IbsnParams.from_buffer_copy(prm)

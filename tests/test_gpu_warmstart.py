@@ -10,6 +10,9 @@ weight gradients sum a few hundred rows per partial before a sum over
 partials).  Adam is elementwise float32: 1e-6 relative.
 """
 
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -257,5 +260,12 @@ def test_warm_start_gain_over_zero_start(G, trained):
     print(f"\nwarm start on {N_HELD} held-out problems: used {used}, Sinkhorn iterations {sk_plain} -> {sk_warm}, "
           f"outer {sum(r[3] for r in rows)} -> {sum(r[4] for r in rows)}, "
           f"seconds {sum(r[5] for r in rows):.3f} -> {sum(r[6] for r in rows):.3f}")
+    rec = os.environ.get("IBSN_RECORD_DIR")
+    if rec:  # keep the measured saving for the record
+        with open(os.path.join(rec, "warmstart_gain_128.json"), "w") as f:
+            json.dump({"held_out": N_HELD, "used": used, "sinkhorn_plain": sk_plain, "sinkhorn_warm": sk_warm,
+                       "rows": rows}, f)
     assert used >= 1
-    assert sk_warm <= sk_plain
+    # the judged start saves Sinkhorn warm-up iterations in total (and never
+    # loses the optimum, checked above)
+    assert sk_warm < sk_plain, (sk_plain, sk_warm)
