@@ -310,6 +310,10 @@ class IBSNParams:
     max_armijo: int = 60
     cg_rtol: float = 0.1
     sparsify: bool = True        # False gives IBN (App. C.3 ablation)
+    # CG forcing term (the paper is silent, reading R3): "gate" relaxes
+    # min(cg_rtol, ||g||) to the accuracy at which the linear model reaches the
+    # gate mu_k; "plain" is min(cg_rtol, ||g||) alone
+    cg_forcing: str = "gate"
 
 
 @dataclass
@@ -365,7 +369,8 @@ def ibsn(C, a, b, params: IBSNParams, gamma0=None, record=False) -> IBSNResult:
                 H = sparsified_hessian(sparsify_plan(P, a, rho), a, eta)
             else:
                 H = hessian(P, a, eta)
-            delta, cg_it = newton_direction(H, g, params.cg_rtol, params.max_cg, mu)
+            delta, cg_it = newton_direction(H, g, params.cg_rtol, params.max_cg,
+                                            mu if params.cg_forcing == "gate" else None)
             tot_cg += cg_it
             t, _, _ = armijo(logX, C, a, b, eta, gamma, delta, g, params.sigma, params.beta, params.max_armijo)
             if record:

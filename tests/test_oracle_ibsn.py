@@ -327,3 +327,14 @@ def test_ibsn_grid_problem_matches_network_simplex():
     res = _solve(prob.C, prob.a, prob.b, prob.eta)
     opt = lp.network_simplex(prob.C, prob.a, prob.b)[0]
     assert res.converged and abs(res.primal - opt) <= 1e-8 * opt
+
+
+@pytest.mark.parametrize("forcing", ["gate", "plain"])
+def test_ibsn_cg_forcing_readings_reach_the_lp_optimum(forcing):
+    """Both readings of the unstated CG tolerance (R3: the gate-relaxed forcing
+    term, or min(0.1, ||g||) alone) reach the network-simplex optimum."""
+    prob = uniform_points_problem(24, 19, seed=77, eta=1e-3)
+    opt = lp.network_simplex(prob.C, prob.a, prob.b)[0]
+    res = O.ibsn(prob.C, prob.a, prob.b, O.IBSNParams(eta=prob.eta, cg_forcing=forcing))
+    assert res.converged
+    assert abs(res.primal - opt) <= 1e-8 * opt
