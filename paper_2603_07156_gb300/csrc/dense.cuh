@@ -63,6 +63,7 @@ struct DenseArgs {
   const float* gam32;      // certify: float copy of gamma
   const float* v3lo;       // certify: v3d - v3 (float-float lo part)
   const double* bounds;    // certify: [0] max |C|, [1] max |gamma| (device)
+  const double* zeta_in;   // certify, grid cost: the c-transform zeta_i, computed beforehand
   // float-float anchor build: w_j as hi + lo floats, lam as hi + lo floats
   const float* wvh;
   const float* wvl;
@@ -908,6 +909,7 @@ __global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
 // the column sums sum_i a_i P_ij change by less than n 2^-64 < 1e-15 relative.
 // ===========================================================================
 constexpr float kFFKeep = 0x1p-64f;
+constexpr float kFFLogKeep = -44.3614195558365f;  // log(2^-64)
 template <int TG, int CH>
 struct FFRow {
   static constexpr int V = 4;
@@ -1049,6 +1051,21 @@ __global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
   }
 }
 
+// bit s * V + e set for each entry whose exponent exceeds the row shift mx by
+// more than log_keep (the entries with exp(x - mx) > keep; no exp needed)
+template <int TG, int CH>
+__device__ __forceinline__ unsigned kept_mask_log(const Tile<float, TG, CH>& t, float mx, float log_keep) {
+  static_assert(CH * 4 <= 32, "one bit per entry of the tile");
+  const float thr = mx + log_keep;
+  unsigned mk = 0u;
+#pragma unroll
+  for (int s = 0; s < CH; ++s)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (t.x[s][e] > thr) mk |= 1u << (s * 4 + e);
+  return mk;
+}
+
 // bit s * V + e set for each entry of the thread's tile above `keep`
 template <int TG, int CH>
 __device__ __forceinline__ unsigned kept_mask(const Tile<float, TG, CH>& t, float keep) {
@@ -1124,8 +1141,7 @@ __global__ void __launch_bounds__(TG) k_plan_ff(DenseArgs<float> A) {
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
-    t.exp_shift(mx);  // float32 filter values
-    const unsigned kept = kept_mask<TG, CH>(t, kFFKeep);
+    const unsigned kept = kept_mask_log<TG, CH>(t, mx, kFFLogKeep);  // float32 filter
     // kept entries: one copy of the float-float code, looped over the mask
     KeptCache kc;
     FF S[1] = {FF{0.f, 0.f}};
@@ -1176,13 +1192,12 @@ __global__ void __launch_bounds__(TG) k_armijo_ff(DenseArgs<float> A) {
   RowStream<float> rs;
   rs.start(A, dyn_sm, s_mbar, r0, r1);
   // an entry can grow by exp(t max|Delta|/eta) at the trial point: keep more
-  const float keep = kFFKeep * (float)A.s2;
+  const float log_keep = A.s2 > 0.0 ? kFFLogKeep + (float)log(A.s2) : -__builtin_huge_valf();
   Tile<float, TG, CH> t;
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
-    t.exp_shift(mx);
-    const unsigned kept = kept_mask<TG, CH>(t, keep);
+    const unsigned kept = kept_mask_log<TG, CH>(t, mx, log_keep);
     KeptCache kc;
     FF S[2] = {FF{0.f, 0.f}, FF{0.f, 0.f}};
     for (unsigned mk = kept; mk != 0u; mk &= mk - 1u) {
@@ -1251,10 +1266,11 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
   for (int i = r0; i < r1; ++i) {
     if (!rs.row(t, A, i, r1)) return;
     const float mx = block_max<TG>(t.local_max(), sht);
-    t.exp_shift(mx);
-    // sweep 1 (every entry, float32): c-transform scan and, for dense costs,
-    // the rank-one sum; the kept entries' float-float work runs from the mask
-    const unsigned kept = kept_mask<TG, CH>(t, kFFKeep);
+    // sweep 1 (every entry, float32): c-transform scan (not for the grid cost,
+    // whose c-transform comes in exactly from the separable computation) and,
+    // for dense and point costs, the rank-one sum; the kept entries'
+    // float-float work runs from the mask
+    const unsigned kept = kept_mask_log<TG, CH>(t, mx, kFFLogKeep);
     float z32 = __builtin_huge_valf(), ceh = 0.f, cel = 0.f;
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
@@ -1262,6 +1278,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         if (c + e >= A.n) continue;
+        if (KIND == 2) continue;  // grid: no scan and no rank-one sum here
         const float2 C = cost_ff(cost, i, c + e, csh, csl);
         z32 = fminf(z32, C.x - A.gam32[c + e]);
         if (rank1) {
@@ -1282,6 +1299,10 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
       R[0] = ff_add(R[0], ev);
     }
     block_sum_ffv<TG, 2>(R, shf);
+    double zeta;
+    if constexpr (KIND == 2) {
+      zeta = A.zeta_in[i];
+    } else {
     const float m32 = -block_max<TG>(-z32, sht);
     double zc = kInf;
     if (z32 <= m32 + zbound) {  // only threads holding a candidate: mark, then re-evaluate in float64
@@ -1300,7 +1321,8 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
         zc = fmin(zc, cost_at(cost, i, j) - A.gam[j]);
       }
     }
-    const double zeta = block_min_exact<TG>(zc, shl);
+    zeta = block_min_exact<TG>(zc, shl);
+    }
     // sweep 2 (kept entries): e_r, the plan part of the primal, complementarity, column sums
     FF Q[4] = {FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}};
     if (kept != 0u) {

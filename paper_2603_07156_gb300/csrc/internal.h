@@ -147,6 +147,10 @@ cudaError_t launch_certify_cols(int64_t n, const double* b, const double* colF, 
 cudaError_t launch_validate_marginals(int64_t m, int64_t n, const double* a, const double* b, double* scal,
                                       cudaStream_t st);
 cudaError_t launch_split_coords(int64_t count, const double* x, float2* out, cudaStream_t st);
+// zeta_i = min_j C_ij - gamma_j for the h x w grid cost C = s * squared bin distance
+// (hmin: h*w doubles of scratch)
+cudaError_t launch_ctransform_grid(int h, int w, double s, const double* gam, double* hmin, double* zeta,
+                                   cudaStream_t st);
 cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ldc, int kind, const double* px,
                                  const double* py, int dim, double scale, double* scal,
                                  cudaStream_t st);

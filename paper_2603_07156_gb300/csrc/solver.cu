@@ -157,7 +157,7 @@ struct ibsn_ctx {
   float* Klo = nullptr;     // lo plane of the float-float anchored matrix
   double* K64 = nullptr;    // float64 anchored matrix (plain float64 mode)
   double *Gam, *gam, *ganc, *dd, *c, *c2, *g, *delta, *logb, *wv, *colF;
-  double *lse, *lse2, *er, *zeta;
+  double *lse, *lse2, *er, *zeta, *zgrid;
   double *rowS0, *rowS1, *rowM;  // per-row results of the float-float passes
   double* rowbuf;                // 6 x m per-row results of the float-float certificate
   int* gridrc;                   // grid cost: bin coordinates per column (null otherwise)
@@ -243,7 +243,7 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   X->K64 = X->have_f64 ? cv.take<double>((size_t)m * ldk) : nullptr;
   double** nvec[] = {&X->Gam, &X->gam, &X->ganc, &X->dd, &X->c, &X->c2, &X->g, &X->delta, &X->logb, &X->wv, &X->colF};
   for (double** v : nvec) *v = cv.take<double>(n);
-  double** mvec[] = {&X->lse, &X->lse2, &X->er, &X->zeta, &X->rowS0, &X->rowS1, &X->rowM};
+  double** mvec[] = {&X->lse, &X->lse2, &X->er, &X->zeta, &X->zgrid, &X->rowS0, &X->rowS1, &X->rowM};
   for (double** v : mvec) *v = cv.take<double>(m);
   X->a32 = cv.take<float>(m);
   X->alo32 = cv.take<float>(m);
@@ -355,6 +355,7 @@ struct PassIn {
   double s1 = 0.0, s2 = 0.0;
   double *rowout = nullptr, *rowout2 = nullptr, *plan_out = nullptr;
   const double* gam = nullptr;
+  const double* zeta_in = nullptr;
   bool sparsify = false, reanchor = false;
   double lam = 0.0;
 };
@@ -416,6 +417,7 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
   A.rowout2 = in.rowout2;
   A.plan_out = in.plan_out;
   A.gam = in.gam;
+  A.zeta_in = in.zeta_in;
   if (in.sparsify) {
     A.pool_col = X->sp.pool_col;
     A.pool_val = (T*)X->sp.pool_val;
@@ -714,8 +716,15 @@ int do_certify(ibsn_ctx* X, Cert* out, double* plan, double* zeta) {
   in.rowout = zeta ? zeta : X->zeta;
   in.rowout2 = X->er;
   in.plan_out = plan;
-  if (mode_for(X, Pass::Certify) == Mode::FF)
+  if (mode_for(X, Pass::Certify) == Mode::FF) {
     CK(launch_certify_prep(X->n, X->gam, X->gam32, X->gamlo32, X->scal, rb(X), X->st));
+    if (X->cost.kind == IBSN_COST_GRID2D) {
+      // exact c-transform of the grid cost by separability (colF is free until the pass's finish)
+      CK(launch_ctransform_grid((int)(X->m / X->cost.gw), X->cost.gw, X->cost.scale, X->gam, X->colF, X->zgrid,
+                                X->st));
+      in.zeta_in = X->zgrid;
+    }
+  }
   RT(run_pass(X, Pass::Certify, in, &g));
   if (mode_for(X, Pass::Certify) == Mode::FF) {
     CK(launch_rows_cert(X->m, X->a, X->rowbuf, X->gridrc, X->cost.scale, in.rowout, in.rowout2, X->scal, rb(X),

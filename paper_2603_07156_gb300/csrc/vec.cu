@@ -582,6 +582,44 @@ cudaError_t launch_validate_marginals(int64_t m, int64_t n, const double* a, con
   note_launch();
   return cudaGetLastError();
 }
+// c-transform zeta_i = min_j C_ij - gamma_j of the grid cost (App. C.1) by
+// separability: with C = s ((r_i - r_j)^2 + (c_i - c_j)^2),
+//   zeta(r, c) = min_{r'} [ s (r - r')^2 + h(r', c) ],
+//   h(r', c) = min_{c'} [ s (c - c')^2 - gamma(r', c') ],
+// the same minimum as the scan over all n bins (it differs only in rounding
+// order), at 2 w h (h + w) float64 operations instead of (h w)^2.
+__global__ void k_ctransform_grid_cols(int h, int w, double s, const double* __restrict__ gam, double* __restrict__ hmin) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= h * w) return;
+  const int r = q / w, c = q - r * w;
+  const double* g = gam + (int64_t)r * w;
+  double best = kInf;
+  for (int c2 = 0; c2 < w; ++c2) {
+    const double d = (double)(c - c2);
+    best = fmin(best, s * (d * d) - g[c2]);
+  }
+  hmin[q] = best;
+}
+__global__ void k_ctransform_grid_rows(int h, int w, double s, const double* __restrict__ hmin, double* __restrict__ zeta) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= h * w) return;
+  const int r = q / w, c = q - r * w;
+  double best = kInf;
+  for (int r2 = 0; r2 < h; ++r2) {
+    const double d = (double)(r - r2);
+    best = fmin(best, s * (d * d) + hmin[(int64_t)r2 * w + c]);
+  }
+  zeta[q] = best;
+}
+cudaError_t launch_ctransform_grid(int h, int w, double s, const double* gam, double* hmin, double* zeta,
+                                   cudaStream_t st) {
+  const unsigned nb = (unsigned)((h * w + 255) / 256);
+  k_ctransform_grid_cols<<<nb, 256, 0, st>>>(h, w, s, gam, hmin);
+  k_ctransform_grid_rows<<<nb, 256, 0, st>>>(h, w, s, hmin, zeta);
+  note_launch(2);
+  return cudaGetLastError();
+}
+
 // coordinates as float pairs (hi, lo) with hi + lo = x to 2^-48 relative
 __global__ void k_split_coords(int64_t count, const double* __restrict__ x, float2* __restrict__ out) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -263,3 +263,31 @@ def test_grid_wide_newton_direction(prec):
         assert r <= 1e-5 * np.linalg.norm(g) + 1e-5 * np.linalg.norm(A, 2) * np.linalg.norm(d), (r, it)
     assert abs(d.sum()) <= 1e-12 * np.abs(d).sum()
     assert g @ d < 0
+
+
+@pytest.mark.parametrize("hw", [(40, 40), (128, 128), (37, 52)])
+def test_grid_ctransform_separable(hw):
+    """The certificate's c-transform for the grid cost, computed through the
+    separability of the squared grid distance, against the scan over all bins
+    of App. C.1 (numpy, float64): equal up to rounding order."""
+    import paper_2603_07156_gb300 as G
+    from workloads import grid_marginals
+    h, w = hw
+    a, b, scale = grid_marginals(h, w, seed=3)
+    n = h * w
+    eta = 1e-3
+    rng = np.random.default_rng(h * w)
+    gamma = rng.normal(0.0, 0.05, n)
+    gp = G.Problem(a=_t(a), b=_t(b), eta=eta, grid=(h, w), cost_scale=scale)
+    ctx = G.Context(gp, G.params(precision="mixed"))
+    ctx.set_state(1, None, _t(gamma), "ff")
+    cert = ctx.certify(want_plan=False)
+    z = cert["zeta"].cpu().numpy()
+    gam = ctx.gamma().cpu().numpy()
+    idx = np.arange(n)
+    zref = np.empty(n)
+    for r0 in range(0, n, 2048):
+        rows = idx[r0:r0 + 2048]
+        C = ((rows[:, None] // w - idx[None, :] // w) ** 2 + (rows[:, None] % w - idx[None, :] % w) ** 2) * scale
+        zref[r0:r0 + 2048] = (C - gam[None, :]).min(axis=1)
+    assert np.abs(z - zref).max() <= 1e-15 * (1.0 + np.abs(gam).max())
