@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--recompute", action="store_true",
+                    help="grid: passes rebuild the anchored exponent from the cost (no stored m x n matrix)")
     ap.add_argument("--no-eta3", dest="eta3", action="store_false",
                     help="skip the extra mixed solve of the grid workload at eta = 1e-3")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -290,7 +292,8 @@ def grid_config(args, world: int) -> dict:
     h = args.grid
     m = h * h
     return {"workload": f"grid{h}x{h} smoothed random fields ({m} bins), eta={args.eta}, "
-                        f"C = squared grid distance / max rebuilt on the fly",
+                        f"C = squared grid distance / max rebuilt on the fly"
+                        + (", anchored exponent rebuilt in every pass (no stored matrix)" if args.recompute else ""),
             "m": m, "n": m, "eta": args.eta, "precision": args.precision, "gap_tol": 1e-8,
             "l2": "inputs larger than L2 (anchored matrix 1 GiB f32 / 2 GiB f64), no flush",
             "parallelism": f"replicas x{world}"}
@@ -807,6 +810,8 @@ def main():
         extra["max_outer"] = args.max_outer
     if args.nnz_cap > 0:
         extra["nnz_cap"] = args.nnz_cap
+    if args.recompute:
+        extra["recompute"] = 1
     prm = G.params(precision=args.precision, profile=1, verbose=args.verbose, **extra)
     ws = G.alloc_workspace(prob, prm)
     stream = torch.cuda.current_stream(dev)

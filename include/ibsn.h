@@ -115,7 +115,10 @@ typedef struct ibsn_params {
                                 solution of that subproblem; primal/dual/rel_gap
                                 certify its rounded plan for the LP of Eq. 1; status
                                 IBSN_OK when the gradient test passed.  0 = IBSN. */
-  int32_t reserved_;
+  int32_t recompute;         /* mixed precision only: 1 = store no anchored exponent
+                                matrix; every pass rebuilds K_ij from the cost with the
+                                arithmetic of the anchor build (identical values, no
+                                m x n workspace; ALU instead of HBM traffic).  0 = stored K */
 } ibsn_params;
 
 /* Result of ibsn_solve.  Output vectors are optional caller buffers. */

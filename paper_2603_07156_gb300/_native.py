@@ -36,7 +36,7 @@ class IbsnParams(C.Structure):
         ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
         ("max_sinkhorn", C.c_int32), ("max_armijo", C.c_int32), ("precision", C.c_int32),
         ("polish", C.c_int32), ("sparsify", C.c_int32), ("verbose", C.c_int32), ("profile", C.c_int32),
-        ("eot_gtol", C.c_double), ("eot", C.c_int32), ("reserved_", C.c_int32),
+        ("eot_gtol", C.c_double), ("eot", C.c_int32), ("recompute", C.c_int32),
     ]
 
 

@@ -64,6 +64,12 @@ struct DenseArgs {
   const float* v3lo;       // certify: v3d - v3 (float-float lo part)
   const double* bounds;    // certify: [0] max |C|, [1] max |gamma| (device)
   const double* zeta_in;   // certify, grid cost: the c-transform zeta_i, computed beforehand
+  // no stored anchored matrix: every pass rebuilds K_ij from the cost, the
+  // anchor-time w = (wvh, wvl), lam = (lamh, laml) and the row shifts rowMa,
+  // with the arithmetic of the anchor pass (bitwise the same values)
+  int recompute;
+  int rc_lo;               // the anchor is the polish's (two planes): hi as it stores it, lo used
+  float* rowMa;            // m anchor row shifts (written by the anchor pass, read by the others)
   // float-float anchor build: w_j as hi + lo floats, lam as hi + lo floats
   const float* wvh;
   const float* wvl;
@@ -289,6 +295,7 @@ struct RowStream {
   // A.stages row buffers of ldk floats
   __device__ __forceinline__ void start(const DenseArgs<T>& A, double* dyn, unsigned long long* mbar, int r0, int r1) {
     if constexpr (std::is_same<T, float>::value) {
+      if (A.recompute) return;  // rows are rebuilt from the cost: nothing to copy
       buf = reinterpret_cast<float*>(dyn);
       bar0 = smem_u32(mbar);
       ns = A.stages > 1 ? kMaxRowStages : 1;
@@ -309,6 +316,10 @@ struct RowStream {
   template <int TG, int CH>
   __device__ __forceinline__ bool row(Tile<T, TG, CH>& t, const DenseArgs<T>& A, int i, int r1) {
     if constexpr (std::is_same<T, float>::value) {
+      if (A.recompute) {
+        rebuild_row(t, A, i);
+        return true;
+      }
       const int q = (i - base) & (ns - 1);
       const bool ok = mbar_wait_parity(bar0 + 8u * (uint32_t)q, (parity >> q) & 1u);
       parity ^= 1u << q;
@@ -910,11 +921,17 @@ __global__ void __launch_bounds__(TG) k_export(DenseArgs<T> A) {
 // ===========================================================================
 constexpr float kFFKeep = 0x1p-64f;
 constexpr float kFFLogKeep = -44.3614195558365f;  // log(2^-64)
+__device__ __forceinline__ FF anchored_ff(const DenseArgs<float>& A, int i, int64_t j);
+
 template <int TG, int CH>
 struct FFRow {
   static constexpr int V = 4;
   // float64 exponent of entry (s, e) of row i relative to the shift M
   __device__ __forceinline__ static double x64(const DenseArgs<float>& A, int i, int64_t c, int e, double M) {
+    if (A.recompute) {
+      const FF k = anchored_ff(A, i, c + e);
+      return ((double)k.hi + (double)k.lo) + A.dv64[c + e] - M;
+    }
     const int64_t off = (int64_t)i * A.ldk + c + e;
     const double lo = A.Klo != nullptr ? (double)__ldg(A.Klo + off) : 0.0;  // no lo plane: float32 K
     return ((double)__ldg(A.K + off) + lo) + A.dv64[c + e] - M;
@@ -986,6 +1003,39 @@ __device__ __forceinline__ void ff_acc(float& sh, float& sl, float x) {
 // offsets d_j move within [-16, 16] (the anchor is rebuilt beyond that).
 constexpr float kFFLoBand = 144.f;
 
+// Anchored exponent (hi, lo) of entry (i, j) exactly as k_reanchor_ff writes
+// it (hi: the float plane; lo: the polish's lo plane, 0 outside the polish),
+// for passes that rebuild it instead of reading the stored planes.
+__device__ __forceinline__ FF anchored_ff(const DenseArgs<float>& A, int i, int64_t j) {
+  if (j >= A.n) return FF{-__builtin_huge_valf(), 0.f};
+  const float Mi = A.rowMa[i];
+  const float csh = (float)A.cost.scale, csl = (float)(A.cost.scale - (double)csh);
+  const float2 C = cost_ff(A.cost, i, j, csh, csl);
+  const float p = A.lamh * C.x;
+  const float pl = fmaf(A.lamh, C.x, -p) + fmaf(A.lamh, C.y, A.laml * C.x);
+  const FF d = ff_add(FF{__ldg(A.wvh + j), __ldg(A.wvl + j)}, FF{-p, -pl});
+  FF k = ff_add(FF{d.hi, d.lo}, FF{-Mi, 0.f});
+  if (!A.rc_lo) return FF{k.hi, 0.f};
+  if (k.hi > -kFFLoBand) {
+    const double K64 = (A.wv[j] - A.lam * cost_at(A.cost, i, j)) - (double)Mi;
+    k.hi = (float)K64;
+    k.lo = (float)(K64 - (double)k.hi);
+  }
+  return k;
+}
+
+// A row of x = K + d rebuilt from the cost (recompute mode of the row stream).
+template <int TG, int CH>
+__device__ __forceinline__ void rebuild_row(Tile<float, TG, CH>& t, const DenseArgs<float>& A, int i) {
+#pragma unroll
+  for (int s = 0; s < CH; ++s) {
+    const int64_t c = Tile<float, TG, CH>::col(s);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      t.x[s][e] = c + e < A.ldk ? anchored_ff(A, i, c + e).hi + A.dv[c + e] : -__builtin_huge_valf();
+  }
+}
+
 // Anchor build (float planes): E_ij = w_j - lam C_ij in float-float (error
 // about 2^-46 |lam C_ij|, far below the float32 plane's rounding), row shift
 // M_i = max_j hi(E_ij), K32 = fl32(E - M).  In the polish (Klo_out set) the
@@ -1023,6 +1073,8 @@ __global__ void __launch_bounds__(TG) k_reanchor_ff(DenseArgs<float> A) {
       }
     }
     mx = block_max<TG>(mx, sht);
+    if (A.rowMa != nullptr && threadIdx.x == 0) A.rowMa[i] = mx;
+    if (A.Kout == nullptr) continue;  // recompute mode: the row shift is all the anchor keeps
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<float, TG, CH>::col(s);
@@ -1105,9 +1157,14 @@ struct KeptCache {
 // float-float exponent x_ij - mx of entry (s, e) of row i: K_hi + K_lo (K_lo
 // absent in float32 mode) + d (hi + lo) - mx
 __device__ __forceinline__ FF ff_x(const DenseArgs<float>& A, int i, int64_t c, int e, float mx) {
-  const int64_t off = (int64_t)i * A.ldk + c + e;
-  const float kl = A.Klo != nullptr ? __ldg(A.Klo + off) : 0.f;
-  const FF x = ff_add(FF{__ldg(A.K + off), kl}, FF{A.dv[c + e], A.dvlo[c + e]});
+  FF k;
+  if (A.recompute) {
+    k = anchored_ff(A, i, c + e);
+  } else {
+    const int64_t off = (int64_t)i * A.ldk + c + e;
+    k = FF{__ldg(A.K + off), A.Klo != nullptr ? __ldg(A.Klo + off) : 0.f};
+  }
+  const FF x = ff_add(k, FF{A.dv[c + e], A.dvlo[c + e]});
   return ff_add(x, FF{-mx, 0.f});
 }
 

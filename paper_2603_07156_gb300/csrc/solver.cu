@@ -139,6 +139,8 @@ struct ibsn_ctx {
   int nsm = 1;
   int istar = 0;
   bool have_f32 = false, have_f64 = false, have_ff = false;
+  bool recompute = false;  // no stored anchored matrix (params.recompute)
+  double lam = 0.0;        // (k+1)/eta of the current anchor
   // state
   int64_t k = 0;
   int prec = 0;            // 0 float64 passes, 1 float32 passes, 2 float-float polish
@@ -163,6 +165,7 @@ struct ibsn_ctx {
   int* gridrc;                   // grid cost: bin coordinates per column (null otherwise)
   float2 *xs, *ys;               // point cost: coordinates as float pairs (null otherwise)
   float* alo32;                  // a - fl32(a)
+  float* rowMa;                  // anchor row shifts (recompute mode)
   float *d32, *em32, *a32, *gam32, *wvh, *wvl;
   float *dlo32, *emlo32, *gamlo32;  // float-float lo parts
   double *d64, *em64;
@@ -238,8 +241,10 @@ void carve(ibsn_ctx* X, Carver& cv, const ibsn_problem* pr, const ibsn_params* p
   const int nbcap = X->nbcap;
   const int64_t cap = pp->nnz_cap > 0 ? pp->nnz_cap : m * n;
   X->have_ff = ff_needed(pp);
-  X->K32 = X->have_f32 ? cv.take<float>((size_t)m * ldk) : nullptr;
-  X->Klo = X->have_ff ? cv.take<float>((size_t)m * ldk) : nullptr;
+  X->recompute = pp->recompute != 0 && X->have_f32;
+  X->K32 = X->have_f32 && !X->recompute ? cv.take<float>((size_t)m * ldk) : nullptr;
+  X->Klo = X->have_ff && !X->recompute ? cv.take<float>((size_t)m * ldk) : nullptr;
+  X->rowMa = cv.take<float>(m);
   X->K64 = X->have_f64 ? cv.take<double>((size_t)m * ldk) : nullptr;
   double** nvec[] = {&X->Gam, &X->gam, &X->ganc, &X->dd, &X->c, &X->c2, &X->g, &X->delta, &X->logb, &X->wv, &X->colF};
   for (double** v : nvec) *v = cv.take<double>(n);
@@ -429,13 +434,23 @@ DenseArgs<T> make_args(ibsn_ctx* X, const PassIn& in) {
     A.cap = X->sp.cap;
     A.err = X->err;
   }
-  if (in.reanchor) {
+  if (in.reanchor || X->recompute) {
+    // the anchor-time w and lam: inputs of the anchor pass, and in recompute
+    // mode of every pass (they rebuild K from them)
+    const double lam = in.reanchor ? in.lam : X->lam;
     A.wv = X->wv;
     A.wvh = X->wvh;
     A.wvl = X->wvl;
-    A.lam = in.lam;
-    A.lamh = (float)in.lam;
-    A.laml = (float)(in.lam - (double)A.lamh);
+    A.lam = lam;
+    A.lamh = (float)lam;
+    A.laml = (float)(lam - (double)A.lamh);
+  }
+  if (X->recompute) {
+    A.recompute = 1;
+    A.rc_lo = X->prec == 2 ? 1 : 0;
+    A.rowMa = X->rowMa;
+  }
+  if (in.reanchor && !X->recompute) {
     if constexpr (F) {
       A.Kout = X->K32;
       A.Klo_out = X->prec == 2 ? X->Klo : nullptr;
@@ -451,9 +466,10 @@ double pass_bytes(ibsn_ctx* X, Pass p, Mode md) {
   const double mn = (double)X->m * (double)X->n;
   // bytes of C read per entry: dense kinds only (grid and point costs are rebuilt on the fly)
   const double sc = X->cost.kind == 0 ? 8.0 : (X->cost.kind == 1 ? 4.0 : 0.0);
-  const double sk = md == Mode::F64 ? 8.0 : 4.0;
+  const double sk = md == Mode::F64 ? 8.0 : (X->recompute ? 0.0 : 4.0);
   switch (p) {
-    case Pass::Reanchor: return mn * ((X->prec == 2 ? 8.0 : (md == Mode::F64 ? 8.0 : 4.0)) + sc);
+    case Pass::Reanchor:
+      return mn * ((X->recompute ? 0.0 : (X->prec == 2 ? 8.0 : (md == Mode::F64 ? 8.0 : 4.0))) + sc);
     case Pass::Certify: return mn * (sk + sc);
     default: return mn * sk;
   }
@@ -493,6 +509,7 @@ int do_reanchor(ibsn_ctx* X) {
   PassIn in;
   in.reanchor = true;
   in.lam = (double)(X->k + 1) / X->eta;
+  X->lam = in.lam;
   RT(run_pass(X, Pass::Reanchor, in));
   X->reanchors++;
   return IBSN_OK;
@@ -822,6 +839,7 @@ int ctx_create_impl(const ibsn_problem* pr, const ibsn_params* pp, void* ws, siz
   RT(check_problem(pr));
   if (!pp || !out) return IBSN_ERR_INVALID_ARG;
   if (pp->precision != IBSN_PREC_FP64 && pp->precision != IBSN_PREC_MIXED) return IBSN_ERR_INVALID_ARG;
+  if (pp->recompute && pp->precision != IBSN_PREC_MIXED) return IBSN_ERR_INVALID_ARG;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return IBSN_ERR_WORKSPACE;
   const int nsm = device_sm_count();
   ibsn_ctx* X = new ibsn_ctx();
@@ -983,6 +1001,7 @@ void ibsn_params_default(ibsn_params* p) {
   p->verbose = 0;
   p->eot = 0;
   p->eot_gtol = 1e-9;
+  p->recompute = 0;
 }
 
 int ibsn_workspace_size(const ibsn_problem* prob, const ibsn_params* params, size_t* bytes) {

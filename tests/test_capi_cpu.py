@@ -41,7 +41,7 @@ int main(void) {
   printf("sizeof ibsn_params %zu\n", sizeof(ibsn_params));
   printf("sizeof ibsn_result %zu\n", sizeof(ibsn_result));
   F(ibsn_problem, eta); F(ibsn_problem, cost_kind); F(ibsn_problem, grid_w); F(ibsn_problem, dim); F(ibsn_problem, x); F(ibsn_problem, y);
-  F(ibsn_params, gamma0); F(ibsn_params, nnz_cap); F(ibsn_params, max_outer); F(ibsn_params, profile); F(ibsn_params, eot_gtol); F(ibsn_params, eot);
+  F(ibsn_params, gamma0); F(ibsn_params, nnz_cap); F(ibsn_params, max_outer); F(ibsn_params, profile); F(ibsn_params, eot_gtol); F(ibsn_params, eot); F(ibsn_params, recompute);
   F(ibsn_result, primal); F(ibsn_result, outer_iters); F(ibsn_result, status); F(ibsn_result, dense_passes);
   F(ibsn_result, kernel_launches); F(ibsn_result, pass_ms); F(ibsn_result, pass_calls); F(ibsn_result, pass_bytes);
   printf("sizeof ibsn_ws_batch %zu\n", sizeof(ibsn_ws_batch));
