@@ -921,6 +921,14 @@ def main():
     roof = {"kernel": dname, "bound": "hbm", "achieved": d_gbs, "peak": hbm, "unit": "GB/s",
             "frac": d_gbs / hbm, "traffic": None, "peak_source": hbm_src,
             "bytes_per_launch": d_bytes, "avg_launch_ms": d_avg_ms}
+    if dname.startswith("pcg"):
+        # the persistent CG is bound by its synchronisation latency: time per
+        # iteration against a floor of two cluster barriers per iteration
+        # (0.7 us each, measured on the cluster kernel)
+        cg_total = sum(r["cg_iters"] for r in results)
+        us = dv["ms"] * 1e3 / max(cg_total, 1)
+        roof["latency"] = {"us_per_cg_iter": us, "floor_us": 1.4, "frac": 1.4 / us if us > 0 else None,
+                           "cg_iters_per_direction": cg_total / max(sum(r["newton_iters"] for r in results), 1)}
     plan = prof.get("plan_f32") or prof.get("plan_f64")
     plan_pass = None
     if plan:
