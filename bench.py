@@ -9,12 +9,14 @@ in HBM).  The anchored exponent matrix (1 GiB float32 / 2 GiB float64) is
 larger than L2, so no flush is needed between steps.
 
 Also reported: the plain float64 GPU path on the same problem (speedup
-denominator), the plan-pass bandwidth, the roofline of the dominant step,
-an end-to-end time through the public API with host buffers, and the CPU
-oracle on a bounded sample (a reported baseline only).
+denominator) with the mixed result's difference from it, one solve at the
+paper's image eta = 1e-3, the plan-pass bandwidth, the roofline of the
+dominant step (HBM and, for the persistent CG, latency), an end-to-end time
+through the public API with host buffers, and the CPU oracle timed on real
+work on this host's cores (a reported baseline only).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--workload grid|batch64|warmstart]
+       [--workload grid|batch64|warmstart|eot|ablation|sphere|points]
 Under torchrun each rank solves the same problem on its own GPU (replicas).
 """
 
