@@ -471,6 +471,8 @@ def run_warmstart(args):
         outs = G.solve_batch([gpu(p) for p in train[k:k + 32]], prm, threads=args.batch_threads)
         targets += [r["gamma"] for r in outs]
         solved += sum(int(r["converged"]) for r in outs)
+        print(f"training solves {len(targets)}/{len(train)} converged {solved} "
+              f"{time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
     torch.cuda.synchronize(dev)
     t_solves = time.perf_counter() - t0
     batches = []
