@@ -1329,6 +1329,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
     // float-float work runs from the mask
     const unsigned kept = kept_mask_log<TG, CH>(t, mx, kFFLogKeep);
     float z32 = __builtin_huge_valf(), ceh = 0.f, cel = 0.f;
+    int zpos = -1;  // the thread's scan minimum: always re-evaluated when the thread holds a candidate
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int64_t c = Tile<float, TG, CH>::col(s);
@@ -1337,7 +1338,11 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
         if (c + e >= A.n) continue;
         if (KIND == 2) continue;  // grid: no scan and no rank-one sum here
         const float2 C = cost_ff(cost, i, c + e, csh, csl);
-        z32 = fminf(z32, C.x - A.gam32[c + e]);
+        const float zv = C.x - A.gam32[c + e];
+        if (zv < z32) {
+          z32 = zv;
+          zpos = s * V + e;
+        }
         if (rank1) {
           // C e_c / S in float-float: exact product of the hi parts plus the cross terms
           const float vh = A.v3[c + e];
@@ -1363,7 +1368,7 @@ __global__ void __launch_bounds__(TG) k_certify_ff(DenseArgs<float> A) {
     const float m32 = -block_max<TG>(-z32, sht);
     double zc = kInf;
     if (z32 <= m32 + zbound) {  // only threads holding a candidate: mark, then re-evaluate in float64
-      unsigned cand = 0u;
+      unsigned cand = zpos >= 0 ? 1u << zpos : 0u;
 #pragma unroll
       for (int s = 0; s < CH; ++s) {
         const int64_t c = Tile<float, TG, CH>::col(s);

@@ -644,7 +644,7 @@ cudaError_t launch_validate_cost(int64_t m, int64_t n, const void* C, int64_t ld
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(&scal[S_C2SUM], 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  if (kind != 0 && kind != 1) return cudaSuccess;
+  if (kind != 0 && kind != 1 && kind != 3) return cudaSuccess;  // the grid cost needs no check
   k_validate_cost<<<1216, 256, 0, st>>>(m, n, C, ldc, kind, px, py, dim, scale, scal);
   note_launch();
   return cudaGetLastError();
