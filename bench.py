@@ -925,6 +925,13 @@ def main():
     roof = {"kernel": dname, "bound": "hbm", "achieved": d_gbs, "peak": hbm, "unit": "GB/s",
             "frac": d_gbs / hbm, "traffic": None, "peak_source": hbm_src,
             "bytes_per_launch": d_bytes, "avg_launch_ms": d_avg_ms}
+    try:  # DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/)
+        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        if dname in tr:
+            roof["traffic"] = tr[dname]
+            roof["traffic_source"] = "ncu capture of early launches (profiles/pcg_grid16384.md)"
+    except Exception:
+        pass
     if dname.startswith("pcg"):
         # the persistent CG is bound by its synchronisation latency: time per
         # iteration against a floor of two cluster barriers per iteration
