@@ -268,7 +268,7 @@ __device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) 
   }
 }
 
-constexpr int kMaxRowStages = 2;
+constexpr int kMaxRowStages = 3;
 
 template <typename T>
 struct RowStream {
@@ -298,7 +298,7 @@ struct RowStream {
       if (A.recompute) return;  // rows are rebuilt from the cost: nothing to copy
       buf = reinterpret_cast<float*>(dyn);
       bar0 = smem_u32(mbar);
-      ns = A.stages > 1 ? kMaxRowStages : 1;
+      ns = A.stages < 1 ? 1 : (A.stages > kMaxRowStages ? kMaxRowStages : A.stages);
       base = r0;
       if (threadIdx.x == 0) {
         for (int q = 0; q < ns; ++q)
@@ -320,15 +320,16 @@ struct RowStream {
         rebuild_row(t, A, i);
         return true;
       }
-      const int q = (i - base) & (ns - 1);
+      const int q = (i - base) % ns;
       const bool ok = mbar_wait_parity(bar0 + 8u * (uint32_t)q, (parity >> q) & 1u);
       parity ^= 1u << q;
       if (ok) t.load_smem(buf + (int64_t)q * A.ldk, A.dv, A.ldk);
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
           if (A.scal != nullptr) A.scal[S_DEVERR] = 1.0;
-          if (ns > 1 && i + 1 < r1) {
-            const int q2 = (i + 1 - base) & (ns - 1);
+          // the copies of rows i+1 .. i+ns-1 may still be in flight: wait for them (bounded)
+          for (int k = 1; k < ns && i + k < r1; ++k) {
+            const int q2 = (i + k - base) % ns;
             mbar_wait_parity(bar0 + 8u * (uint32_t)q2, (parity >> q2) & 1u);
           }
         }

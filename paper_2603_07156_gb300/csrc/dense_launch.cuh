@@ -43,9 +43,9 @@ struct TileTable<double> {
   static constexpr int ch[count] = {2, 4, 4, 8, 8, 8};
 };
 
-// Shared memory up to which a float pass keeps two row buffers (a 16384-wide
-// float row is 64 KiB; two leave room on the SM for the L1 cache).
-constexpr size_t kTwoStageSmemMax = 160 * 1024;
+// Shared memory a float pass may give its ring of row buffers (a 16384-wide
+// float row is 64 KiB: three fit below the 227 KiB a CTA can have).
+constexpr size_t kRowRingSmemMax = 200 * 1024;
 
 // The stop-test pass holds no column accumulators, so its float tiles take
 // twice the threads (half the chunks per thread) from the third configuration
@@ -107,8 +107,9 @@ cudaError_t launch_dense_t(Pass p, DenseArgs<T>& A, int nsm, cudaStream_t st, Pa
   if (std::is_same<T, double>::value) {
     if (pass_uses_colacc(p)) smem = (size_t)A.ldk * sizeof(double);
   } else if (p != Pass::Reanchor) {
-    // two row copies in flight per block when both buffers fit comfortably
-    A.stages = 2 * (size_t)A.ldk * sizeof(float) <= kTwoStageSmemMax ? 2 : 1;
+    // as many row copies in flight per block (up to three) as the ring's budget holds
+    const size_t row = (size_t)A.ldk * sizeof(float);
+    A.stages = 3 * row <= kRowRingSmemMax ? 3 : (2 * row <= kRowRingSmemMax ? 2 : 1);
     smem = (size_t)A.stages * (size_t)A.ldk * sizeof(float);
   }
   // one-time opt-in to large dynamic shared memory, and cached occupancy
