@@ -77,6 +77,7 @@ def parse():
                          "paper's Square EOT setting; ablation: IBSN against IBN (dense Hessian)")
     ap.add_argument("--sizes", default="", help="eot/ablation: comma-separated m = n values")
     ap.add_argument("--batch-threads", type=int, default=8)
+    ap.add_argument("--sequential", action="store_true", help="batch64: also time the problems one by one")
     ap.add_argument("--verbose", type=int, default=0, help="per-outer log lines of the solver on stderr")
     return ap.parse_args()
 
@@ -398,8 +399,9 @@ def run_batch(args):
     prm = G.params(precision="mixed", **extra)
     wss = [G.alloc_workspace(p, prm) for p in probs]
     entries = sum(int(p.a.numel()) * int(p.b.numel()) for p in probs)
-    for _ in range(max(args.warmup, 1)):
-        G.solve_batch(probs[:8], prm, threads=args.batch_threads, workspaces=wss[:8])
+    for _ in range(max(args.warmup, 1)):  # warm-up on the 8 smallest problems
+        small = sorted(range(len(probs)), key=lambda q: probs[q].a.numel() * probs[q].b.numel())[:8]
+        G.solve_batch([probs[q] for q in small], prm, threads=args.batch_threads, workspaces=[wss[q] for q in small])
     barrier(world)
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(dev.index if dev.index is not None else 0) if rank == 0 else None
@@ -414,11 +416,13 @@ def run_batch(args):
     barrier(world)
     clk = clocks.stop() if clocks else None
     rep = replica_line_fields(statistics.mean(times), world)
-    t0 = time.perf_counter()
-    for p, w in zip(probs, wss):
-        G.solve(p, prm, workspace=w)
-    torch.cuda.synchronize(dev)
-    t_seq = time.perf_counter() - t0
+    t_seq = None
+    if args.sequential:  # the same problems one after another on one stream, for comparison
+        t0 = time.perf_counter()
+        for p, w in zip(probs, wss):
+            G.solve(p, prm, workspace=w)
+        torch.cuda.synchronize(dev)
+        t_seq = time.perf_counter() - t0
     if rank != 0:
         return
     gaps = [r["rel_gap"] for r in out]
@@ -431,7 +435,10 @@ def run_batch(args):
                                "(rebuilt on the fly from the points), random marginals, seeds 100..163, eta=1e-4",
                    "entries": entries, "threads": args.batch_threads, "precision": "mixed",
                    "l2": "64 problems' data far larger than L2, no flush", "parallelism": f"replicas x{world}"},
-        "sequential_s": t_seq, "batch_speedup": t_seq / rep["value"],
+        "sequential_s": t_seq, "batch_speedup": t_seq / rep["value"] if t_seq else None,
+        "outer_iters": {"mean": statistics.mean(r["outer_iters"] for r in out),
+                        "max": max(r["outer_iters"] for r in out)},
+        "solve_s": {"mean": statistics.mean(r["seconds"] for r in out), "max": max(r["seconds"] for r in out)},
         "converged": sum(1 for r in out if r["converged"]), "max_rel_gap": max(gaps),
         "timing": "host wall clock around the call (the call ends with every stream synchronised)",
         "clocks": clk,
