@@ -175,8 +175,9 @@ int ibsn_solve(const ibsn_problem* prob, const ibsn_params* params, void* worksp
  * from ibsn_workspace_size for probs[q]) and fills results[q] (its status in
  * results[q].status), exactly as ibsn_solve(&probs[q], params, ...) would:
  * the results are identical to solving the problems one by one.  The solves
- * run concurrently: `threads` host threads (<= 0: 8) take problems in index
- * order, each issuing its problems' kernels on its own stream (streams[q]
+ * run concurrently: `threads` host threads (<= 0: 8) take problems largest
+ * first (by m n; ties in index order), each issuing its problems' kernels on
+ * its own stream (streams[q]
  * when `streams` is not null, otherwise a stream the thread creates and
  * destroys), so passes of different problems overlap on the GPU.  Runs on the
  * calling thread's current device.  Returns IBSN_OK when every problem

@@ -1153,13 +1153,22 @@ int ibsn_solve_batch(int count, const ibsn_problem* probs, const ibsn_params* pa
   const int nt = std::max(1, std::min(threads > 0 ? threads : 8, count));
   std::atomic<int> next{0};
   std::vector<int> codes((size_t)count, IBSN_OK);
+  // largest problems first (by m n), so that no large solve starts last and
+  // leaves the other threads idle; each problem's result does not depend on
+  // the order
+  std::vector<int> order((size_t)count);
+  for (int q = 0; q < count; ++q) order[(size_t)q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (double)probs[x].m * (double)probs[x].n > (double)probs[y].m * (double)probs[y].n;
+  });
   auto worker = [&]() {
     if (cudaSetDevice(dev) != cudaSuccess) return;
     cudaStream_t own = nullptr;
     if (!streams && cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) own = nullptr;
     for (;;) {
-      const int q = next.fetch_add(1);
-      if (q >= count) break;
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int q = order[(size_t)k];
       void* st = streams ? streams[q] : (void*)own;
       codes[(size_t)q] = ibsn_solve(&probs[q], params, workspaces[q], workspace_bytes[q], &results[q], st);
     }
