@@ -43,9 +43,11 @@ struct TileTable<double> {
   static constexpr int ch[count] = {2, 4, 4, 8, 8, 8};
 };
 
-// Shared memory a float pass may give its ring of row buffers (a 16384-wide
-// float row is 64 KiB: three fit below the 227 KiB a CTA can have).
-constexpr size_t kRowRingSmemMax = 200 * 1024;
+// Shared memory a float pass may give its ring of row buffers.  A 16384-wide
+// float row is 64 KiB; two buffers (two copies in flight) measured fastest:
+// a third (192 KiB) left too little L1 for the per-column vectors the passes
+// read with every row (plan pass 3966 against 4674 GB/s).
+constexpr size_t kRowRingSmemMax = 160 * 1024;
 
 // The stop-test pass holds no column accumulators, so its float tiles take
 // twice the threads (half the chunks per thread) from the third configuration

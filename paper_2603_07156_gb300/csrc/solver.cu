@@ -776,6 +776,7 @@ int do_certify(ibsn_ctx* X, Cert* out, double* plan, double* zeta) {
 
 struct NewtonStats {
   int newton = 0, cg = 0, armijo = 0;
+  int fallbacks = 0;  // steps taken along -g because the Newton direction gave none
   int64_t max_nnz = 0;
 };
 
@@ -800,24 +801,50 @@ int newton_step(ibsn_ctx* X, const ibsn_params& P, double gate, int k, int v, Ne
   if (P.verbose > 1)
     fprintf(stderr, "[ibsn]   newton k=%d v=%d |g|=%.3e nnz=%lld maxrow=%d maxcol=%d cg=%d rtol=%.1e\n", k, v, gn,
             (long long)X->nnz, (int)X->h_scal[S_MAXROW], (int)X->h_scal[S_MAXCOL], cgit, rtol);
-  // trials whose largest exponent change t max|Delta|/eta exceeds the pass
-  // range are rejected unevaluated (exp would overflow in that precision)
-  const double dmax = X->h_scal[S_DELTAMAX];
+  // Backtracking along the stored direction.  Trials whose largest exponent
+  // change t max|Delta|/eta exceeds the pass range are rejected unevaluated
+  // (exp would overflow in that precision).  Returns 0 when a step met the
+  // Armijo condition, 1 when only the last trial gave a finite decrease
+  // (taken, reading R4), 2 when no usable step was found.
   const double range = X->prec == 0 ? 600.0 : (X->prec == 1 ? 60.0 : 30.0);
   double t = 1.0, dL = 0.0, slope = 0.0;
-  bool evaluated = false;
-  for (int tr = 0; tr < P.max_armijo; ++tr) {
-    const bool last = tr + 1 == P.max_armijo;
-    if (t * dmax <= range || last) {
-      RT(do_armijo_trial(X, t, &dL, &slope));
-      evaluated = true;
-      ++ns->armijo;
-      if (std::isfinite(dL) && dL <= P.sigma * t * slope) break;
+  auto backtrack = [&](int* outcome) -> int {
+    const double dmax = X->h_scal[S_DELTAMAX];
+    t = 1.0;
+    bool evaluated = false;
+    for (int tr = 0; tr < P.max_armijo; ++tr) {
+      const bool last = tr + 1 == P.max_armijo;
+      if (t * dmax <= range || last) {
+        RT(do_armijo_trial(X, t, &dL, &slope));
+        evaluated = true;
+        ++ns->armijo;
+        if (std::isfinite(dL) && dL <= P.sigma * t * slope) {
+          *outcome = 0;
+          return IBSN_OK;
+        }
+      }
+      if (!last) t *= P.beta;
     }
-    if (!last) t *= P.beta;
+    *outcome = (evaluated && std::isfinite(dL) && dL < 0.0) ? 1 : 2;
+    return IBSN_OK;
+  };
+  int outcome = 2;
+  RT(backtrack(&outcome));
+  if (outcome == 2) {
+    if (!(gn > 0.0) || !std::isfinite(gn)) return IBSN_ERR_NUMERICAL;
+    // no usable step along the Newton direction (a non-finite or non-descent
+    // direction): fall back to the steepest-descent direction -g, scaled to an
+    // exponent change of at most 1 at t = 1, and backtrack again
+    CK(cudaMemsetAsync(X->delta, 0, sizeof(double) * X->n, X->st));
+    k_axpy<<<(unsigned)((X->n + 255) / 256), 256, 0, X->st>>>(X->n, -X->eta / gn, X->g, X->delta);
+    note_launch();
+    CK(cudaGetLastError());
+    CK(launch_dir_post(X->n, X->eta, X->delta, X->g, X->scal, rb(X), X->st));
+    RT(read_scal(X));
+    ++ns->fallbacks;
+    RT(backtrack(&outcome));
+    if (outcome == 2) return IBSN_ERR_NUMERICAL;
   }
-  // after max_armijo trials the last step tried is taken (reading R4)
-  if (!evaluated || !std::isfinite(dL)) return IBSN_ERR_NUMERICAL;
   RT(do_accept(X, t));
   if (!std::isfinite(X->gn)) return IBSN_ERR_NUMERICAL;
   ++ns->newton;
