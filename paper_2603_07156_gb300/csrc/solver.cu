@@ -805,7 +805,8 @@ int newton_step(ibsn_ctx* X, const ibsn_params& P, double gate, int k, int v, Ne
   // change t max|Delta|/eta exceeds the pass range are rejected unevaluated
   // (exp would overflow in that precision).  Returns 0 when a step met the
   // Armijo condition, 1 when only the last trial gave a finite decrease
-  // (taken, reading R4), 2 when no usable step was found.
+  // (taken, reading R4: near the solution rounding can make every trial's
+  // decrease slightly positive), 2 when no trial gave a finite value.
   const double range = X->prec == 0 ? 600.0 : (X->prec == 1 ? 60.0 : 30.0);
   double t = 1.0, dL = 0.0, slope = 0.0;
   auto backtrack = [&](int* outcome) -> int {
@@ -825,15 +826,16 @@ int newton_step(ibsn_ctx* X, const ibsn_params& P, double gate, int k, int v, Ne
       }
       if (!last) t *= P.beta;
     }
-    *outcome = (evaluated && std::isfinite(dL) && dL < 0.0) ? 1 : 2;
+    *outcome = (evaluated && std::isfinite(dL)) ? 1 : 2;
     return IBSN_OK;
   };
   int outcome = 2;
   RT(backtrack(&outcome));
   if (outcome == 2) {
     if (!(gn > 0.0) || !std::isfinite(gn)) return IBSN_ERR_NUMERICAL;
-    // no usable step along the Newton direction (a non-finite or non-descent
-    // direction): fall back to the steepest-descent direction -g, scaled to an
+    // no finite trial along the Newton direction (a non-finite direction, or
+    // one whose smallest trial still overflows): fall back to the
+    // steepest-descent direction -g, scaled to an
     // exponent change of at most 1 at t = 1, and backtrack again
     CK(cudaMemsetAsync(X->delta, 0, sizeof(double) * X->n, X->st));
     k_axpy<<<(unsigned)((X->n + 255) / 256), 256, 0, X->st>>>(X->n, -X->eta / gn, X->g, X->delta);
