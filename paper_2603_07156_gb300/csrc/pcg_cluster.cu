@@ -95,9 +95,8 @@ __device__ __forceinline__ int cl_ld_int(uint32_t a) {
 __device__ __forceinline__ void cl_st(uint32_t a, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
-__device__ __forceinline__ void cl_st4(uint32_t a, float4 v) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-               : "memory");
+__device__ __forceinline__ void cl_st2(uint32_t a, float x, float y) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
 }
 __device__ __forceinline__ void cl_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -125,44 +124,58 @@ __device__ __forceinline__ int cta_scan_excl(int v, int* sh, int* total) {
   return base + x - v;
 }
 
-// CTA sum of six floats: float within a warp, float-float across the CTA's
-// warps; the record (12 floats, hi/lo pairs) lands in rec (lane 0 of warp 0).
-__device__ __forceinline__ void cta_sum6(const float (&v)[6], float* sh, float* rec) {
+// CTA sums of six floats, pushed into slot `rank` of every CTA's receive
+// buffer.  Within a warp the six values (padded to eight) are reduced by
+// recursive halving: at each of the first three exchange steps a lane sends
+// half of the quantities it still holds and keeps the other half, so a warp
+// issues 9 shuffles instead of 30 and lane l ends with the warp total of
+// quantity l / 4 (float, as a plain warp sum).  Warps 0..5 then sum quantity
+// q over the CTA's 32 warps in float-float, and lane r of warp q writes the
+// (hi, lo) pair into CTA r's buffer.
+__device__ __forceinline__ void cta_sum6_push(const float (&v)[6], float* sh, float* recv, uint32_t rank,
+                                              uint32_t cs) {
   constexpr int NW = kClT / 32;
+  static_assert(NW == 32, "one warp partial per lane");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float f[6];
+  float x[4];
+  {
+    const bool up = (lane & 16) != 0;  // keeps quantities 4..7 (0..3 otherwise; 6, 7 are zero)
 #pragma unroll
-  for (int q = 0; q < 6; ++q) f[q] = warp_sum(v[q]);
-  if (lane == 0) {
+    for (int p = 0; p < 2; ++p) {
+      const float send = up ? v[p] : v[p + 4];
+      const float keep = up ? v[p + 4] : v[p];
+      x[p] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
 #pragma unroll
-    for (int q = 0; q < 6; ++q) sh[q * NW + w] = f[q];
-  }
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const FF t = warp_sum_ff(FF{sh[q * NW + lane], 0.f});
-      if (lane == 0) {
-        rec[2 * q] = t.hi;
-        rec[2 * q + 1] = t.lo;
-      }
+    for (int p = 2; p < 4; ++p) {
+      const float send = up ? v[p] : 0.f;
+      const float keep = up ? 0.f : v[p];
+      x[p] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
   }
-}
-
-// warp 0: push this CTA's record into slot `rank` of every CTA's receive
-// buffer (lane r writes CTA r's copy)
-__device__ __forceinline__ void push_record(const float* rec, float* recv, uint32_t rank, uint32_t cs) {
-  const uint32_t lane = threadIdx.x & 31;
-  __syncwarp();
-  if (lane < cs) {
-    const float4 v0 = *reinterpret_cast<const float4*>(rec);
-    const float4 v1 = *reinterpret_cast<const float4*>(rec + 4);
-    const float4 v2 = *reinterpret_cast<const float4*>(rec + 8);
-    const uint32_t dst = cl_map(recv + 12 * rank, lane);
-    cl_st4(dst, v0);
-    cl_st4(dst + 16, v1);
-    cl_st4(dst + 32, v2);
+  {
+    const bool up = (lane & 8) != 0;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const float send = up ? x[p] : x[p + 2];
+      const float keep = up ? x[p + 2] : x[p];
+      x[p] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  {
+    const bool up = (lane & 4) != 0;
+    const float send = up ? x[0] : x[1];
+    const float keep = up ? x[1] : x[0];
+    x[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  x[0] += __shfl_xor_sync(0xffffffffu, x[0], 2);
+  x[0] += __shfl_xor_sync(0xffffffffu, x[0], 1);
+  const int qd = lane >> 2;  // quantity this lane now holds
+  if ((lane & 3) == 0 && qd < 6) sh[qd * NW + w] = x[0];
+  __syncthreads();
+  if (w < 6) {
+    const FF tq = warp_sum_ff(FF{sh[w * NW + lane], 0.f});
+    if ((uint32_t)lane < cs) cl_st2(cl_map(recv + 12 * rank + 2 * w, (uint32_t)lane), tq.hi, tq.lo);
   }
 }
 
@@ -181,11 +194,10 @@ __device__ __forceinline__ void cluster_totals(const float* recv, uint32_t cs, F
 __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
   extern __shared__ __align__(16) unsigned char cl_sm[];
   __shared__ float s_red[6 * (kClT / 32)];
-  __shared__ __align__(16) float s_rec[12];              // this CTA's partial record
   __shared__ __align__(16) float s_recv[12 * kClMax];    // every CTA's record, pushed by its owner
   __shared__ int s_flag;                                 // staging overflow (read by every CTA)
   __shared__ int s_scan[kClT / 32];
-  __shared__ float s_a32, s_b32, s_tstar;
+  __shared__ float s_a32, s_b32, s_tstar, s_rtol2, s_astar, s_rr0, s_gam;
   __shared__ int s_done;
   const uint32_t rank = cl_rank(), cs = gridDim.x;
   const int t = threadIdx.x;
@@ -257,16 +269,20 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
   const float ai = (t < nrow) ? A.a32[i] : 0.f;
   {
     const float red[6] = {0.f, 0.f, 0.f, q * dinv * r0, 0.f, 0.f};
-    cta_sum6(red, s_red, s_rec);
-    if (t < 32) push_record(s_rec, s_recv, rank, cs);
+    cta_sum6_push(red, s_red, s_recv, rank, cs);
   }
   __syncthreads();
   cl_sync();  // states, entries and records of every CTA are in place
 
   FF Qr{0.f, 0.f}, Qw{0.f, 0.f}, Qs{0.f, 0.f};
-  float alpha = 0.f, beta = 0.f, gam = 0.f, rr0 = 0.f, rr = 0.f;
-  const float rtol2 = (float)(A.rtol * A.rtol);
-  const float astar = A.a32[A.istar];
+  float rr = 0.f;
+  // thread 0's scalars live in shared memory (1024 threads leave 64 registers each)
+  if (t == 0) {
+    s_rtol2 = (float)(A.rtol * A.rtol);
+    s_astar = A.a32[A.istar];
+    s_rr0 = 0.f;
+    s_gam = 0.f;
+  }
   bool warm = true;
   int it = 0;
   if (t < 32) {
@@ -277,7 +293,7 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
   if (t == 0) {
     s_a32 = 0.f;
     s_b32 = 0.f;
-    s_tstar = astar * Qr.hi;
+    s_tstar = s_astar * Qr.hi;
   }
   __syncthreads();
   const int re0 = (t < nrow) ? s_roff[t] : 0, re1 = (t < nrow) ? s_roff[t + 1] : 0;
@@ -303,7 +319,7 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
     float dsum[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (t < ncol) {
       float acc = 0.f;
-#pragma unroll 4
+#pragma unroll 2
       for (int k = ce0; k < ce1; ++k) {
         const uint2 e = s_ent[k];
         acc += __uint_as_float(e.y) * s_t[e.x];
@@ -326,13 +342,14 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
       dsum[4] = qd * w_new;
       dsum[5] = qd * s_new;
     }
-    cta_sum6(dsum, s_red, s_rec);
-    if (t < 32) push_record(s_rec, s_recv, rank, cs);
+    cta_sum6_push(dsum, s_red, s_recv, rank, cs);
     cl_sync();  // every record has arrived everywhere
     FF tot[6];
     if (t < 32) cluster_totals(s_recv, cs, tot);
     if (t == 0) {
-      // Chronopoulos-Gear update, identical in every CTA
+      // Chronopoulos-Gear update, identical in every CTA; alpha and beta
+      // start from this iteration's values (the loop-top copies a32, b32)
+      float alpha = a32, beta = b32, rr0 = s_rr0, gam = s_gam;
       const float g1 = tot[0].hi;
       const float d1v = tot[1].hi;
       rr = tot[2].hi;
@@ -352,7 +369,7 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
         }
       } else {
         ++it;
-        if (rr <= rtol2 * rr0 || it >= A.maxit) {
+        if (rr <= s_rtol2 * rr0 || it >= A.maxit) {
           done = 1;
         } else {
           beta = g1 / gam;
@@ -365,11 +382,13 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
           }
         }
       }
+      s_rr0 = rr0;
+      s_gam = gam;
       s_done = done;
       s_a32 = alpha;
       s_b32 = beta;
       const FF qu = ff_add(Qr, ff_neg(ff_mul_f(ff_add(Qw, ff_mul_f(Qs, beta)), alpha)));
-      s_tstar = astar * qu.hi;
+      s_tstar = s_astar * qu.hi;
     }
     __syncthreads();
     if (s_done) break;
@@ -377,7 +396,7 @@ __global__ void __launch_bounds__(kClT, 1) k_pcg_cluster(PcgClArgs A) {
   if (t < ncol) A.x_out[j] = (double)s_x[t];
   if (rank == 0 && t == 0) {
     A.scal[S_CG_ITERS] = (double)it;
-    A.scal[S_CG_RES] = rr0 > 0.f ? sqrt((double)rr / (double)rr0) : 0.0;
+    A.scal[S_CG_RES] = s_rr0 > 0.f ? sqrt((double)rr / (double)s_rr0) : 0.0;
   }
   cl_sync();  // no CTA leaves while another may still write or read its shared memory
 }
