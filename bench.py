@@ -953,7 +953,9 @@ def main():
         tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
         if dname in tr:
             roof["traffic"] = tr[dname]
-            roof["traffic_source"] = "ncu capture of early launches (profiles/pcg_grid16384.md)"
+            roof["traffic_source"] = ("ncu DRAM counters of the grid-wide k_pcg32 launches of the early outer "
+                                      "steps (profiles/pcg_grid16384.md); the cluster kernel of the later "
+                                      "steps reads DRAM only to stage its entries")
     except Exception:
         pass
     if dname.startswith("pcg"):
