@@ -156,6 +156,29 @@ def test_newton_direction_solves_shifted_system_and_descends():
     assert g @ delta < 0                        # descent direction (Lemma B.6 (i))
 
 
+def test_pcg_finite_termination_on_three_eigenvalues():
+    """Conjugate gradients in exact arithmetic end after as many iterations as
+    the (preconditioned) matrix has distinct eigenvalues.  A symmetric
+    circulant matrix has a constant diagonal, so the Jacobi preconditioner is
+    a scalar and keeps the three eigenvalues chosen here; a sign or index slip
+    in the recurrence loses this property."""
+    n = 16
+    lam = np.ones(n)
+    lam[0] = 5.0
+    lam[[1, 7, 9, 15]] = 2.0                    # symmetric in j <-> n - j: real circulant
+    c = np.real(np.fft.ifft(lam))
+    A = np.array([[c[(j - i) % n] for j in range(n)] for i in range(n)])
+    assert np.allclose(A, A.T) and np.allclose(np.diag(A), c[0])
+    rhs = np.random.default_rng(5).normal(size=n)
+    x, it, res = O.pcg(A, rhs, np.diag(A).copy(), 1e-10, 50)
+    assert it == 3
+    assert res <= 1e-10 * np.linalg.norm(rhs)
+    assert np.abs(x - np.linalg.solve(A, rhs)).max() <= 1e-12 * np.abs(x).max()
+    # two iterations leave a residual of the size of the data
+    _, it2, res2 = O.pcg(A, rhs, np.diag(A).copy(), 1e-10, 2)
+    assert it2 == 2 and res2 > 1e-3 * np.linalg.norm(rhs)
+
+
 def test_armijo_accepts_sufficient_decrease():
     C, a, b, eta, logX, gamma = _state(seed=22)
     P = O.plan(logX, C, eta, gamma)
