@@ -193,6 +193,15 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def blas_threads() -> int:
+    """Threads this process's oracle work may use: numpy's elementwise passes
+    run on one thread, its BLAS calls on at most OPENBLAS_NUM_THREADS."""
+    try:
+        return max(1, int(os.environ.get("OPENBLAS_NUM_THREADS", "1")))
+    except ValueError:
+        return 1
+
+
 def oracle_job(name: str, h: int, eta: float) -> dict:
     """Real oracle work timed on the host (runs in a child process whose BLAS
     thread count is set by its environment).
@@ -367,7 +376,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_pass * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": grid_config(args, 1), "value_basis": "estimate scaled from the timed steps",
-            "cpu_baseline": {"value": v, "unit": "s", "cores": host_cores(), "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": blas_threads(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
