@@ -1452,7 +1452,6 @@ template <int TG, int CH>
 __global__ void __launch_bounds__(TG) k_export_ff(DenseArgs<float> A) {
   extern __shared__ __align__(128) double dyn_sm[];
   __shared__ unsigned long long s_mbar[kMaxRowStages];
-  __shared__ double shd[2 * (TG / 32)];
   __shared__ float shf[8 * (TG / 32)];
   __shared__ float sht[TG / 32];
   constexpr int V = 4;

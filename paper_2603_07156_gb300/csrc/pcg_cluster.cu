@@ -82,11 +82,6 @@ __device__ __forceinline__ float4 cl_ld4(uint32_t a) {
                : "memory");
   return v;
 }
-__device__ __forceinline__ float cl_ld(uint32_t a) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
-  return v;
-}
 __device__ __forceinline__ int cl_ld_int(uint32_t a) {
   int v;
   asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
